@@ -1,0 +1,21 @@
+"""FP64 CPU oracle of the particle-mesh lensing forward model and its adjoint.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this package:
+only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may use it.  It shares no code with the CUDA path; the only common
+module is ``pm_inputs`` (seeded inputs, no arithmetic of the method).
+
+Every step is written plainly in float64 with numpy/scipy primitives (FFT,
+quadrature, ODE integration, interpolation), following the paper's method:
+
+* Eq. (conv) and the lensing kernel q(chi) -- Born convergence (``lightcone``)
+* Sec. 3 (package design) -- FastPM kick/drift stepping, box replication with
+  rotation, the sub-evolution projection, PGD sharpening (``nbody``,
+  ``lightcone``, ``mesh``)
+* Appendix A -- comoving distance integral, Eisenstein-Hu linear power,
+  finite-difference cosmology derivatives (``cosmology``, ``adjoint``)
+
+Readings of points the paper leaves open are stated in each function's
+docstring.  Parity unpinned: absolute Eisenstein-Hu transfer values (only
+limits and the sound-horizon fit pin them).
+"""

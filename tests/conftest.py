@@ -1,0 +1,23 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the built CUDA library")
+    config.addinivalue_line("markers", "slow: long-running oracle case")
+
+
+@pytest.fixture(scope="session")
+def cuda_lib():
+    """The CUDA library through its C ABI; GPU tests fail loudly without it."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2012_07266_gb300 import lib
+    return lib.load()
