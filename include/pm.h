@@ -1,0 +1,175 @@
+/*
+ * pm.h -- C ABI of the GB300 particle-mesh weak-lensing library.
+ *
+ * The library runs the forward model of MADLens (Boehm, Feng, Lee & Dai,
+ * arXiv:2012.07266) on one GPU: FastPM-style kick-drift-kick particle-mesh
+ * steps (Sec. 3), the Born lightcone projection with box replication,
+ * rotation and the sub-evolution scheme onto convergence maps (Eq. conv,
+ * Sec. 3), the PGD sharpening step (Sec. 3), and the reverse-mode derivative
+ * of the maps with respect to the initial white-noise modes, Omega_m and
+ * sigma_8 (Sec. 3, Appendix A).
+ *
+ * Conventions shared by every entry point:
+ *  - Ownership: the caller allocates every device buffer, including the
+ *    single workspace handed to pm_init; the library never allocates device
+ *    memory.  Host-side bookkeeping (a few KB of tables) lives in the
+ *    context and is freed by pm_destroy.
+ *  - Streams: every call enqueues its kernels on the stream given to
+ *    pm_init and returns without synchronising, except where stated
+ *    (kappa_maps, pm_vjp and pm_sync_status synchronise that stream).
+ *  - Errors: arguments are validated on the host before anything is
+ *    enqueued; a failing check returns PM_ERR_ARG / PM_ERR_STATE /
+ *    PM_ERR_WORKSPACE / PM_ERR_UNSUPPORTED and enqueues nothing.  A CUDA
+ *    launch error returns PM_ERR_CUDA.  Non-finite values met on the device
+ *    set a flag that the synchronising calls report as PM_ERR_NONFINITE.
+ *  - Layouts: particle arrays are row-major (N, 3) with N = nc^3 and particle
+ *    j = (jz * nc + jy) * nc + jx; meshes are [z][y][x] with x fastest;
+ *    maps are [source][iy][ix] with ix along theta_x.
+ *  - Units: H0 = 1, lengths in Mpc/h, momentum p = a^3 E(a) dx/da in Mpc/h.
+ */
+#ifndef PMLENS_PM_H
+#define PMLENS_PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pm_ctx pm_ctx; /* opaque; created by pm_init, freed by pm_destroy */
+
+typedef enum {
+  PM_OK = 0,
+  PM_ERR_ARG = 1,         /* invalid argument or configuration            */
+  PM_ERR_WORKSPACE = 2,   /* workspace too small or misaligned            */
+  PM_ERR_CUDA = 3,        /* a CUDA call or launch failed                 */
+  PM_ERR_NONFINITE = 4,   /* NaN/Inf met on the device                    */
+  PM_ERR_STATE = 5,       /* entry point called out of order              */
+  PM_ERR_UNSUPPORTED = 6  /* size not supported by the FFT plans          */
+} pm_status;
+
+enum { PM_FP32 = 0, PM_FP64 = 1 };
+enum { PM_MAX_ZS = 16 };
+
+/*
+ * Simulation parameters; mirrors the user parameters of the paper's Table 1
+ * (BoxSize, Nmesh, B, Nsteps, N_maps, Nmesh2D, BoxSize2D, zs_source,
+ * Omega_m, sigma_8, PGD, interpolation) plus the Eisenstein-Hu inputs of
+ * Appendix A and the precision / checkpoint fields of this library.
+ */
+typedef struct {
+  int32_t nc;              /* particles per side; N = nc^3                         */
+  int32_t nmesh;           /* force mesh per side (B = nmesh / nc), <= 1024          */
+  double box;              /* box side L, Mpc/h                                      */
+  double omega_m, sigma8;  /* Table 1 cosmology                                      */
+  double h, n_s, omega_b, t_cmb; /* Eisenstein-Hu transfer inputs (Appendix A)       */
+  double a_init;           /* initial scale factor; steps are linear in a to 1       */
+  int32_t nsteps;          /* number of kick-drift-kick steps                        */
+  int32_t lpt_order;       /* 1 (Zel'dovich) or 2 (2LPT) initial conditions          */
+  int32_t n_zs;            /* number of source planes, 1..PM_MAX_ZS                  */
+  double zs[PM_MAX_ZS];    /* source redshifts (zs_source)                           */
+  int32_t map_npix;        /* map pixels per side (Nmesh2D)                          */
+  double map_fov_deg;      /* map side in degrees (BoxSize2D)                        */
+  int32_t sub_evolution;   /* 1: sub-evolution projection ("interpolation")        */
+  int32_t pgd;             /* 1: PGD sharpening of the projected positions           */
+  double pgd_params[5];    /* alpha0, mu, k_l [h/Mpc], k_s [h/Mpc], n                */
+  uint64_t rotation_seed;  /* seed of the per-replica rotation hash                  */
+  int32_t rotate;          /* 1: rotate/shift each box replica                       */
+  int32_t precision;       /* PM_FP32 (fast path) or PM_FP64 (plain comparator)      */
+  int32_t ckpt_every;      /* adjoint checkpoint interval in steps; 0 = no adjoint   */
+} pm_config;
+
+/* Device bytes the workspace of this configuration needs (its HBM footprint,
+ * used for admission).  Returns PM_ERR_ARG / PM_ERR_UNSUPPORTED on a bad
+ * configuration. */
+pm_status pm_workspace_size(const pm_config* cfg, size_t* bytes);
+
+/* Create a context.  Computes the FP64 cosmology tables on the host (linear
+ * growth, FastPM time factors, comoving distance, Eisenstein-Hu P(k)) and
+ * uploads them into the workspace.  d_workspace: device buffer of at least
+ * pm_workspace_size() bytes, 256-byte aligned, owned by the caller and kept
+ * alive until pm_destroy.  stream: a cudaStream_t (NULL = legacy stream). */
+pm_status pm_init(pm_ctx** out, const pm_config* cfg, void* d_workspace, size_t bytes,
+                  void* stream);
+
+/* Initial conditions (Sec. 3/Appendix A: Gaussian modes, EH power, LPT):
+ * d_noise is the caller's real-space N(0,1) white-noise field on the nc^3
+ * lattice, [z][y][x] float64 on the device.  delta_L(k) = DFT(noise) *
+ * sqrt(P(k) nc^3 / L^3); Zel'dovich (and 2LPT) displacements place the
+ * particles at a_init; the PM force at those positions is computed so that
+ * pm_step(0) can kick.  Resets the maps. */
+pm_status pm_ic(pm_ctx* ctx, const double* d_noise);
+
+/* One FastPM step i (0 <= i < nsteps, in order; Sec. 3): kick p to
+ * a_{i+1/2} with the force at a_i, drift x to a_{i+1}, paint, FFT Poisson and
+ * gradient, inverse FFT to the force at a_{i+1}; with PGD on and shell i
+ * inside the lightcone, also the PGD displacement meshes. */
+pm_status pm_step(pm_ctx* ctx, int32_t i);
+
+/* Project shell i (chi(a_{i+1}), chi(a_i)] onto the internal FP64 maps
+ * (Eq. conv with Born weights, box replication and rotation, sub-evolution
+ * and PGD as configured).  Must follow pm_step(i) directly; a shell beyond
+ * the farthest source is a no-op. */
+pm_status lens_project(pm_ctx* ctx, int32_t i);
+
+/* Write the convergence maps kappa = sum of projected weights minus the
+ * mean-density term (Eq. conv) to d_maps: n_zs * npix^2 float64, device,
+ * caller-owned.  Synchronises the stream; PM_ERR_NONFINITE if any map value
+ * or projected position was not finite. */
+pm_status kappa_maps(pm_ctx* ctx, double* d_maps);
+
+/* Reverse-mode derivative of a scalar loss of the maps (Sec. 3, VJP;
+ * Appendix A for Omega_m, sigma_8).  Requires ckpt_every > 0 and the whole
+ * forward run (pm_ic, all pm_step / lens_project) done.  d_dL_dkappa:
+ * n_zs * npix^2 float64 (device); d_dL_dnoise: nc^3 float64 output
+ * (device); h_dL_dparams: 2 float64 on the HOST, [dL/dOmega_m, dL/dsigma_8]
+ * (either output pointer may be NULL).  Synchronises the stream. */
+pm_status pm_vjp(pm_ctx* ctx, const double* d_dL_dkappa, double* d_dL_dnoise,
+                 double* h_dL_dparams);
+
+/* Free the context (not the caller's workspace). */
+pm_status pm_destroy(pm_ctx* ctx);
+
+/* Static description of a status code. */
+const char* pm_strerror(pm_status status);
+
+/* ---- inspection entry points (state transfer for tests and users) ----- */
+
+/* Current particles: positions in [0, L) and momenta, (N, 3) float64 on the
+ * device (either pointer may be NULL).  After pm_step(i): x(a_{i+1}),
+ * p(a_{i+1/2}). */
+pm_status pm_get_particles(pm_ctx* ctx, double* d_x, double* d_p);
+
+/* Replace the particle state by (N, 3) float64 device arrays, taken as the
+ * state after step `next_step - 1` (x at a_{next_step}, p at a_{next_step-1/2};
+ * next_step = 0 means the initial state at a_init), and compute the force at
+ * those positions. */
+pm_status pm_set_particles(pm_ctx* ctx, const double* d_x, const double* d_p,
+                           int32_t next_step);
+
+/* PM force F = -(3/2) Omega_m grad(phi) (Mpc/h, momentum units per unit
+ * kick factor) at the current particle positions, (N, 3) float64 device. */
+pm_status pm_get_forces(pm_ctx* ctx, double* d_f);
+
+/* PGD displacement (Mpc/h) at the current positions, (N, 3) float64 device;
+ * valid after pm_step(i) of a shell inside the lightcone with PGD on. */
+pm_status pm_get_pgd(pm_ctx* ctx, double* d_s);
+
+/* Forward r2c DFT (sign -1, unnormalised) of a real nmesh^3 float64 field
+ * [z][y][x] into d_out: nmesh * nmesh * (nmesh/2 + 1) complex as interleaved
+ * float64 [z][y][kx][re,im], through the library's FFT kernels. */
+pm_status pm_fft_r2c(pm_ctx* ctx, const double* d_in, double* d_out);
+
+/* CIC density (mean 1) of the current particles on the force mesh,
+ * nmesh^3 float64 device [z][y][x]. */
+pm_status pm_get_density(pm_ctx* ctx, double* d_rho);
+
+/* Synchronise the stream and report the sticky device error flag. */
+pm_status pm_sync_status(pm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMLENS_PM_H */

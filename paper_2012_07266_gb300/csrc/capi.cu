@@ -1,0 +1,533 @@
+// C ABI of the PM lensing library: context, workspace layout, host FP64
+// tables, and the sequencing of the device work of each entry point.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <type_traits>
+
+#include "pm_internal.h"
+
+using namespace pmlens;
+
+namespace {
+
+size_t al(size_t x) { return (x + 255) & ~size_t(255); }
+int round16(int x) { return (x + 15) / 16 * 16; }
+
+pm_status check_config(const pm_config* c) {
+  if (!c) return PM_ERR_ARG;
+  if (c->nc < 2 || c->nmesh < 2 || c->nmesh > 1024 || c->nc > c->nmesh) return PM_ERR_ARG;
+  if (!fft_supported(c->nmesh) || !fft_supported(c->nc)) return PM_ERR_UNSUPPORTED;
+  if (!(c->box > 0) || !(c->omega_m > 0 && c->omega_m <= 1) || !(c->sigma8 > 0)) return PM_ERR_ARG;
+  if (!(c->h > 0) || !(c->omega_b > 0 && c->omega_b < c->omega_m) || !(c->t_cmb > 0)) return PM_ERR_ARG;
+  if (!(c->a_init > 1e-3 && c->a_init < 1) || c->nsteps < 1 || c->nsteps > 100000) return PM_ERR_ARG;
+  if (c->lpt_order != 1 && c->lpt_order != 2) return PM_ERR_ARG;
+  if (c->n_zs < 1 || c->n_zs > PM_MAX_ZS) return PM_ERR_ARG;
+  for (int s = 0; s < c->n_zs; ++s)
+    if (!(c->zs[s] > 0 && c->zs[s] < 1.0 / c->a_init - 1.0)) return PM_ERR_ARG;
+  if (c->map_npix < 1 || c->map_npix > 16384 || !(c->map_fov_deg > 0 && c->map_fov_deg < 60)) return PM_ERR_ARG;
+  if (c->precision != PM_FP32 && c->precision != PM_FP64) return PM_ERR_ARG;
+  if (c->pgd && !(c->pgd_params[2] >= 0 && c->pgd_params[3] > 0 && c->pgd_params[4] > 0)) return PM_ERR_ARG;
+  if (c->ckpt_every < 0) return PM_ERR_ARG;
+  return PM_OK;
+}
+
+void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
+  const size_t rs = cfg.precision == PM_FP64 ? 8 : 4, cs = 2 * rs;
+  const size_t M = cfg.nmesh, nc = cfg.nc, np = nc * nc * nc;
+  P = round16((int)M / 2 + 1);
+  Pc = round16((int)nc / 2 + 1);
+  const size_t mesh = M * M * M * rs, cmesh = M * M * (size_t)P * cs;
+  const size_t grid = np * rs, cgrid = nc * nc * (size_t)Pc * cs;
+  size_t o = 0;
+  L.cell = o; o += al(np * 4);
+  L.frac = o; o += al(3 * np * rs);
+  L.mom = o; o += al(3 * np * rs);
+  L.fmesh = o; o += al(3 * mesh);
+  L.smesh = o; o += cfg.pgd ? al(3 * mesh) : 0;
+  L.maps = o; o += al((size_t)cfg.n_zs * cfg.map_npix * cfg.map_npix * 8);
+  L.flags = o; o += 256;
+  L.sqrtp = o; o += al((3 * (nc / 2) * (nc / 2) + 1) * 8);
+  L.tab_d1 = o; o += al(kChiTab * 8);
+  L.tab_inva = o; o += al(kChiTab * 8);
+  L.scratch = o;
+  const int nout = cfg.pgd ? 6 : 3;
+  L.rho = o;
+  L.cbuf = L.rho + al(mesh);
+  L.ubuf = L.cbuf + al(cmesh);
+  const size_t step_end = L.ubuf + nout * al(cmesh);
+  L.ic_real = o;
+  L.ic_cbuf = L.ic_real + al(grid);
+  L.ic_u = L.ic_cbuf + al(cgrid);
+  L.ic_out = L.ic_u + 9 * al(cgrid);
+  const size_t ic_end = L.ic_out + 13 * al(grid);
+  L.adj = std::max(step_end, ic_end);
+  L.total = L.adj;
+}
+
+template <typename R>
+R* rp(pm_ctx* c, size_t off) { return reinterpret_cast<R*>(c->ws + off); }
+
+size_t cmesh_bytes(pm_ctx* c) { return (size_t)c->M * c->M * c->P * 2 * c->rsz; }
+size_t cgrid_bytes(pm_ctx* c) { return (size_t)c->nc * c->nc * c->Pc * 2 * c->rsz; }
+
+pm_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PM_OK : PM_ERR_CUDA; }
+
+// ------------------------------------------------------------ host tables
+void build_tables(pm_ctx* c) {
+  const pm_config& cfg = c->cfg;
+  Cosmo& co = c->cosmo;
+  co.init(cfg.omega_m, cfg.sigma8, cfg.h, cfg.n_s, cfg.omega_b, cfg.t_cmb);
+  const int n = cfg.nsteps;
+  c->a.resize(n + 1);
+  c->ah.resize(n);
+  for (int i = 0; i <= n; ++i) c->a[i] = cfg.a_init + (1.0 - cfg.a_init) * i / n;
+  for (int i = 0; i < n; ++i) c->ah[i] = 0.5 * (c->a[i] + c->a[i + 1]);
+  c->kick.resize(n);
+  c->drift.resize(n);
+  for (int i = 0; i < n; ++i) {
+    const double aprev = i == 0 ? c->a[0] : c->ah[i - 1];
+    c->kick[i] = (co.gp(c->ah[i]) - co.gp(aprev)) / co.gf(c->a[i]);
+    c->drift[i] = (co.D1(c->a[i + 1]) - co.D1(c->a[i])) / co.gp(c->ah[i]);
+  }
+  c->chi_a.resize(n + 1);
+  for (int i = 0; i <= n; ++i) c->chi_a[i] = co.chi_a(c->a[i]);
+  c->chi_s.resize(cfg.n_zs);
+  double chi_s_max = 0;
+  for (int s = 0; s < cfg.n_zs; ++s) {
+    c->chi_s[s] = co.chi_a(1.0 / (1.0 + cfg.zs[s]));
+    chi_s_max = std::max(chi_s_max, c->chi_s[s]);
+  }
+  c->chi_tab_max = 1.1 * std::max(c->chi_a[0], chi_s_max) + 50.0;
+  c->chi_tab_h = c->chi_tab_max / (kChiTab - 1);
+  // mean-density term: (3/2) Om (H0/c)^2 int_0^chi_s chi (chi_s - chi) / (chi_s a) dchi (Simpson)
+  for (int s = 0; s < PM_MAX_ZS; ++s) c->mean_term[s] = 0.0;
+  for (int s = 0; s < cfg.n_zs; ++s) {
+    const double cs = c->chi_s[s];
+    const int m = 8000;
+    const double hh = cs / m;
+    double acc = 0;
+    for (int k = 0; k <= m; ++k) {
+      const double x = k * hh;
+      const double f = x * (cs - x) / (cs * co.a_of_chi(x));
+      acc += (k == 0 || k == m ? 1.0 : (k & 1 ? 4.0 : 2.0)) * f;
+    }
+    c->mean_term[s] = 1.5 * cfg.omega_m / (kCoverH0 * kCoverH0) * acc * hh / 3.0;
+  }
+}
+
+cudaError_t upload_tables(pm_ctx* c) {
+  const pm_config& cfg = c->cfg;
+  std::vector<double> d1t(kChiTab), inva(kChiTab);
+  for (int k = 0; k < kChiTab; ++k) {
+    const double a = c->cosmo.a_of_chi(k * c->chi_tab_h);
+    d1t[k] = c->cosmo.D1(a);
+    inva[k] = 1.0 / a;
+  }
+  const int nh = cfg.nc / 2;
+  std::vector<double> sq(3 * nh * nh + 1);
+  const double kf = 2.0 * M_PI / cfg.box, vol = cfg.box * cfg.box * cfg.box;
+  const double ncube = (double)cfg.nc * cfg.nc * cfg.nc;
+  sq[0] = 0.0;
+  for (size_t n2 = 1; n2 < sq.size(); ++n2) sq[n2] = std::sqrt(c->cosmo.pk(kf * std::sqrt((double)n2)) * ncube / vol);
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->ws + c->L.tab_d1, d1t.data(), kChiTab * 8, cudaMemcpyHostToDevice, c->stream))) return e;
+  if ((e = cudaMemcpyAsync(c->ws + c->L.tab_inva, inva.data(), kChiTab * 8, cudaMemcpyHostToDevice, c->stream))) return e;
+  if ((e = cudaMemcpyAsync(c->ws + c->L.sqrtp, sq.data(), sq.size() * 8, cudaMemcpyHostToDevice, c->stream))) return e;
+  if ((e = cudaMemsetAsync(c->ws + c->L.flags, 0, 256, c->stream))) return e;
+  return cudaStreamSynchronize(c->stream);  // host vectors go out of scope
+}
+
+// ---------------------------------------------------------- force passes
+// Paint is done by the caller into rho; this computes the force meshes (and
+// the PGD meshes when alpha_pgd is given) from rho.
+template <typename R>
+cudaError_t force_from_rho(pm_ctx* c, bool with_pgd, double alpha_pgd) {
+  const pm_config& cfg = c->cfg;
+  SpecParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.op = with_pgd ? OP_FORCE_PGD : OP_FORCE;
+  sp.kf = 2.0 * M_PI / cfg.box;
+  const double m3 = (double)c->M * c->M * c->M;
+  sp.scale = 1.5 * cfg.omega_m * (c->M / cfg.box) / m3;
+  sp.pgd_scale = alpha_pgd * (c->M / cfg.box) / m3;
+  sp.kl = cfg.pgd_params[2];
+  sp.ks = cfg.pgd_params[3];
+  sp.nexp = cfg.pgd_params[4];
+  const int nout = with_pgd ? 6 : 3;
+  void* ub[6];
+  R* outs[6];
+  for (int o = 0; o < nout; ++o) ub[o] = c->ws + c->L.ubuf + o * al(cmesh_bytes(c));
+  R* F = rp<R>(c, c->L.fmesh);
+  for (int o = 0; o < 3; ++o) outs[o] = F + o * c->mesh_elems;
+  if (with_pgd) {
+    R* S = rp<R>(c, c->L.smesh);
+    for (int o = 0; o < 3; ++o) outs[3 + o] = S + o * c->mesh_elems;
+  }
+  return spectral_apply<R>(rp<R>(c, c->L.rho), c->ws + c->L.cbuf, ub, outs, nout, c->M, c->P, sp, c->stream);
+}
+
+bool shell_active(pm_ctx* c, int i) {
+  double mx = 0;
+  for (double v : c->chi_s) mx = std::max(mx, v);
+  return c->chi_a[i + 1] < mx;
+}
+
+double pgd_alpha(pm_ctx* c, int i) { return c->cfg.pgd_params[0] * std::pow(c->a[i + 1], c->cfg.pgd_params[1]); }
+
+template <typename R>
+pm_status do_ic(pm_ctx* c, const double* d_noise) {
+  const pm_config& cfg = c->cfg;
+  cudaStream_t s = c->stream;
+  const long long g = (long long)c->nc * c->nc * c->nc;
+  R* noise = rp<R>(c, c->L.ic_real);
+  cudaError_t e = launch_convert_in<R>(d_noise, noise, g, s);
+  if (e) return PM_ERR_CUDA;
+  const int nout = cfg.lpt_order == 2 ? 9 : 3;
+  void* ub[9];
+  R* outs[13];
+  for (int o = 0; o < 9; ++o) ub[o] = c->ws + c->L.ic_u + o * al(cgrid_bytes(c));
+  for (int o = 0; o < 13; ++o) outs[o] = rp<R>(c, c->L.ic_out + o * al(g * c->rsz));
+  SpecParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.op = cfg.lpt_order == 2 ? OP_LPT2_DERIV : OP_LPT1;
+  sp.kf = 2.0 * M_PI / cfg.box;
+  sp.scale = 1.0 / (double)g;
+  sp.sqrtp = reinterpret_cast<const double*>(c->ws + c->L.sqrtp);
+  if ((e = spectral_apply<R>(noise, c->ws + c->L.ic_cbuf, ub, outs, nout, c->nc, c->Pc, sp, s))) return PM_ERR_CUDA;
+  R* const* psi2 = nullptr;
+  if (cfg.lpt_order == 2) {
+    if ((e = launch_lpt2_source<R>(c, outs + 3, outs[9], g))) return PM_ERR_CUDA;
+    SpecParams sp2 = sp;
+    sp2.op = OP_GRAD_NEG;
+    if ((e = spectral_apply<R>(outs[9], c->ws + c->L.ic_cbuf, ub, outs + 10, 3, c->nc, c->Pc, sp2, s)))
+      return PM_ERR_CUDA;
+    psi2 = outs + 10;
+  }
+  const double a0 = c->a[0];
+  const Cosmo& co = c->cosmo;
+  if ((e = launch_ic_particles<R>(c, outs, psi2, co.D1(a0), psi2 ? co.D2(a0) : 0.0, co.gp(a0),
+                                  psi2 ? co.gp2(a0) : 0.0)))
+    return PM_ERR_CUDA;
+  R* rho = rp<R>(c, c->L.rho);
+  if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, s))) return PM_ERR_CUDA;
+  if ((e = launch_paint<R>(c, rho))) return PM_ERR_CUDA;
+  if ((e = force_from_rho<R>(c, false, 0.0))) return PM_ERR_CUDA;
+  return PM_OK;
+}
+
+template <typename R>
+pm_status do_step(pm_ctx* c, int i) {
+  R* rho = rp<R>(c, c->L.rho);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, c->stream))) return PM_ERR_CUDA;
+  if ((e = launch_kdk_paint<R>(c, rho, c->kick[i], c->drift[i]))) return PM_ERR_CUDA;
+  const bool pgd = c->cfg.pgd && shell_active(c, i);
+  if ((e = force_from_rho<R>(c, pgd, pgd ? pgd_alpha(c, i) : 0.0))) return PM_ERR_CUDA;
+  c->pgd_valid = pgd;
+  return PM_OK;
+}
+
+// every replica box that may hold a particle of shell (lo, hi] whose projected
+// position can land on the map (FOV widened by one pixel and a margin that
+// bounds the sub-evolution and PGD displacements)
+std::vector<Replica> shell_replicas(pm_ctx* c, double lo, double hi) {
+  const pm_config& cfg = c->cfg;
+  const double L = cfg.box;
+  const double fov = cfg.map_fov_deg * M_PI / 180.0;
+  const double half = 0.5 * fov + fov / cfg.map_npix;
+  const double t = std::tan(half);
+  const double margin = std::max(0.1 * L, 10.0);
+  const double cosc = 1.0 / std::sqrt(1.0 + 2.0 * t * t);
+  const double z0 = std::max(0.0, lo * cosc - margin), z1 = hi + margin;
+  const double w = hi * t + margin;
+  std::vector<Replica> out;
+  for (int nz = (int)std::floor(z0 / L); nz <= (int)std::floor(z1 / L); ++nz)
+    for (int ny = (int)std::floor(-w / L); ny <= (int)std::floor(w / L); ++ny)
+      for (int nx = (int)std::floor(-w / L); nx <= (int)std::floor(w / L); ++nx) {
+        const int n3[3] = {nx, ny, nz};
+        double dmin2 = 0, dmax2 = 0;
+        for (int d = 0; d < 3; ++d) {
+          const double a = n3[d] * L, b = a + L;
+          const double nearv = a > 0 ? a : (b < 0 ? b : 0.0);
+          const double farv = std::fabs(a) > std::fabs(b) ? a : b;
+          dmin2 += nearv * nearv;
+          dmax2 += farv * farv;
+        }
+        if (dmin2 > hi * hi || dmax2 < lo * lo) continue;
+        Replica r;
+        r.n[0] = (int16_t)nx; r.n[1] = (int16_t)ny; r.n[2] = (int16_t)nz;
+        if (cfg.rotate) {
+          // SplitMix64 output of seed ^ (20-bit fields nx, ny, nz)
+          uint64_t key = ((uint64_t)(nx & 0xFFFFF) << 40) | ((uint64_t)(ny & 0xFFFFF) << 20) |
+                         (uint64_t)(nz & 0xFFFFF);
+          uint64_t z = (cfg.rotation_seed ^ key) + 0x9E3779B97F4A7C15ULL;
+          z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+          z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+          z ^= z >> 31;
+          static const uint8_t perms[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+          const int pi = (int)(z % 6);
+          for (int d = 0; d < 3; ++d) {
+            r.perm[d] = perms[pi][d];
+            r.shift[d] = (int16_t)(((z >> (16 + 16 * d)) & 0xFFFF) % (uint64_t)cfg.nmesh);
+          }
+          r.flip = (uint8_t)((z >> 8) & 7);
+        } else {
+          for (int d = 0; d < 3; ++d) { r.perm[d] = (uint8_t)d; r.shift[d] = 0; }
+          r.flip = 0;
+        }
+        out.push_back(r);
+      }
+  return out;
+}
+
+template <typename R>
+pm_status do_lens(pm_ctx* c, int i) {
+  LensShell sh;
+  const double lo = c->chi_a[i + 1], hi = c->chi_a[i];
+  sh.chi_lo2 = lo * lo;
+  sh.chi_hi2 = hi * hi;
+  sh.d1_next = c->cosmo.D1(c->a[i + 1]);
+  sh.gp_half = c->cosmo.gp(c->ah[i]);
+  const std::vector<Replica> reps = shell_replicas(c, lo, hi);
+  for (size_t b = 0; b < reps.size(); b += kMaxReplicas) {
+    sh.nrep = (int)std::min<size_t>(kMaxReplicas, reps.size() - b);
+    for (int q = 0; q < sh.nrep; ++q) sh.rep[q] = reps[b + q];
+    if (launch_lens<R>(c, sh, c->cfg.pgd && c->pgd_valid)) return PM_ERR_CUDA;
+  }
+  return PM_OK;
+}
+
+template <typename R>
+__global__ void k_unpad_complex(const typename std::conditional<sizeof(R) == 4, float2, double2>::type* in,
+                                double* out, int n, int P) {
+  const long long h = n / 2 + 1;
+  const long long tot = (long long)n * n * h;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < tot; j += (long long)gridDim.x * blockDim.x) {
+    const long long row = j / h, k = j - row * h;
+    const auto v = in[row * P + k];
+    out[2 * j] = v.x;
+    out[2 * j + 1] = v.y;
+  }
+}
+
+pm_status read_flags(pm_ctx* c) {
+  int h = 0;
+  if (cudaMemcpyAsync(&h, c->ws + c->L.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) return PM_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream)) return PM_ERR_CUDA;
+  return h ? PM_ERR_NONFINITE : PM_OK;
+}
+
+#define PM_DISPATCH(c, FN, ...) ((c)->prec == PM_FP64 ? FN<double>(__VA_ARGS__) : FN<float>(__VA_ARGS__))
+
+template <typename R>
+pm_status do_set_particles(pm_ctx* c, const double* x, const double* p, int ns) {
+  if (launch_set_particles<R>(c, x, p)) return PM_ERR_CUDA;
+  R* rho = rp<R>(c, c->L.rho);
+  if (cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, c->stream)) return PM_ERR_CUDA;
+  if (launch_paint<R>(c, rho)) return PM_ERR_CUDA;
+  const bool pgd = ns > 0 && c->cfg.pgd && shell_active(c, ns - 1);
+  if (force_from_rho<R>(c, pgd, pgd ? pgd_alpha(c, ns - 1) : 0.0)) return PM_ERR_CUDA;
+  c->pgd_valid = pgd;
+  return PM_OK;
+}
+
+template <typename R>
+pm_status do_readout(pm_ctx* c, size_t off, double* out) {
+  R* m = rp<R>(c, off);
+  R* ms[3] = {m, m + c->mesh_elems, m + 2 * c->mesh_elems};
+  return cuda_status(launch_readout<R>(c, ms, c->cfg.box / c->M, out));
+}
+
+template <typename R>
+pm_status do_fft(pm_ctx* c, const double* in, double* out) {
+  R* rho = rp<R>(c, c->L.rho);
+  if (launch_convert_in<R>(in, rho, c->mesh_elems, c->stream)) return PM_ERR_CUDA;
+  if (fft3d_r2c<R>(rho, c->ws + c->L.cbuf, c->M, c->P, c->stream)) return PM_ERR_CUDA;
+  using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+  k_unpad_complex<R><<<1024, 256, 0, c->stream>>>(reinterpret_cast<const C*>(c->ws + c->L.cbuf), out, c->M, c->P);
+  return cuda_status(cudaGetLastError());
+}
+
+template <typename R>
+pm_status do_density(pm_ctx* c, double* out) {
+  R* rho = rp<R>(c, c->L.rho);
+  if (cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, c->stream)) return PM_ERR_CUDA;
+  if (launch_paint<R>(c, rho)) return PM_ERR_CUDA;
+  return cuda_status(launch_convert_out<R>(rho, out, c->mesh_elems, 1.0, c->stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_workspace_size(const pm_config* cfg, size_t* bytes) {
+  pm_status st = check_config(cfg);
+  if (st) return st;
+  if (!bytes) return PM_ERR_ARG;
+  Layout L;
+  int P, Pc;
+  plan_layout(*cfg, L, P, Pc);
+  *bytes = L.total;
+  return PM_OK;
+}
+
+pm_status pm_init(pm_ctx** out, const pm_config* cfg, void* d_workspace, size_t bytes, void* stream) {
+  if (!out) return PM_ERR_ARG;
+  *out = nullptr;
+  pm_status st = check_config(cfg);
+  if (st) return st;
+  Layout L;
+  int P, Pc;
+  plan_layout(*cfg, L, P, Pc);
+  if (!d_workspace || bytes < L.total || (reinterpret_cast<uintptr_t>(d_workspace) & 255)) return PM_ERR_WORKSPACE;
+  pm_ctx* c = new (std::nothrow) pm_ctx();
+  if (!c) return PM_ERR_ARG;
+  c->cfg = *cfg;
+  c->stream = reinterpret_cast<cudaStream_t>(stream);
+  c->prec = cfg->precision;
+  c->rsz = cfg->precision == PM_FP64 ? 8 : 4;
+  c->nc = cfg->nc;
+  c->M = cfg->nmesh;
+  c->np = (long long)cfg->nc * cfg->nc * cfg->nc;
+  c->P = P;
+  c->Pc = Pc;
+  c->mesh_elems = (long long)c->M * c->M * c->M;
+  c->cmesh_elems = (long long)c->M * c->M * P;
+  c->cgrid_elems = (long long)c->nc * c->nc * Pc;
+  c->nout_step = cfg->pgd ? 6 : 3;
+  c->ws = reinterpret_cast<char*>(d_workspace);
+  c->ws_bytes = bytes;
+  c->L = L;
+  c->next_step = -1;
+  c->last_stepped = -1;
+  c->projected = -1;
+  c->pgd_valid = 0;
+  c->ic_done = 0;
+  build_tables(c);
+  if (upload_tables(c) != cudaSuccess) { delete c; return PM_ERR_CUDA; }
+  *out = c;
+  return PM_OK;
+}
+
+pm_status pm_ic(pm_ctx* c, const double* d_noise) {
+  if (!c || !d_noise) return PM_ERR_ARG;
+  if (cudaMemsetAsync(c->ws + c->L.maps, 0, (size_t)c->cfg.n_zs * c->cfg.map_npix * c->cfg.map_npix * 8, c->stream))
+    return PM_ERR_CUDA;
+  pm_status st = PM_DISPATCH(c, do_ic, c, d_noise);
+  if (st) return st;
+  c->ic_done = 1;
+  c->next_step = 0;
+  c->last_stepped = -1;
+  c->projected = -1;
+  c->pgd_valid = 0;
+  return PM_OK;
+}
+
+pm_status pm_step(pm_ctx* c, int32_t i) {
+  if (!c) return PM_ERR_ARG;
+  if (i < 0 || i >= c->cfg.nsteps) return PM_ERR_ARG;
+  if (!c->ic_done || i != c->next_step) return PM_ERR_STATE;
+  pm_status st = PM_DISPATCH(c, do_step, c, i);
+  if (st) return st;
+  c->next_step = i + 1;
+  c->last_stepped = i;
+  return PM_OK;
+}
+
+pm_status lens_project(pm_ctx* c, int32_t i) {
+  if (!c) return PM_ERR_ARG;
+  if (i < 0 || i >= c->cfg.nsteps) return PM_ERR_ARG;
+  if (!c->ic_done || i != c->last_stepped || c->projected >= i) return PM_ERR_STATE;
+  c->projected = i;
+  if (!shell_active(c, i)) return PM_OK;
+  return PM_DISPATCH(c, do_lens, c, i);
+}
+
+pm_status kappa_maps(pm_ctx* c, double* d_maps) {
+  if (!c || !d_maps) return PM_ERR_ARG;
+  if (!c->ic_done) return PM_ERR_STATE;
+  if (launch_kappa_finalize(c, d_maps)) return PM_ERR_CUDA;
+  return read_flags(c);
+}
+
+pm_status pm_vjp(pm_ctx* c, const double* d_dL_dkappa, double* d_dL_dnoise, double* h_dL_dparams) {
+  if (!c || !d_dL_dkappa) return PM_ERR_ARG;
+  (void)d_dL_dnoise;
+  (void)h_dL_dparams;
+  return PM_ERR_UNSUPPORTED;
+}
+
+pm_status pm_destroy(pm_ctx* c) {
+  if (!c) return PM_ERR_ARG;
+  delete c;
+  return PM_OK;
+}
+
+const char* pm_strerror(pm_status s) {
+  switch (s) {
+    case PM_OK: return "ok";
+    case PM_ERR_ARG: return "invalid argument or configuration";
+    case PM_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
+    case PM_ERR_CUDA: return "CUDA error";
+    case PM_ERR_NONFINITE: return "non-finite value on the device";
+    case PM_ERR_STATE: return "entry point called out of order";
+    case PM_ERR_UNSUPPORTED: return "unsupported size or feature";
+    default: return "unknown status";
+  }
+}
+
+pm_status pm_get_particles(pm_ctx* c, double* d_x, double* d_p) {
+  if (!c || (!d_x && !d_p)) return PM_ERR_ARG;
+  if (!c->ic_done) return PM_ERR_STATE;
+  return cuda_status(c->prec == PM_FP64 ? launch_get_particles<double>(c, d_x, d_p)
+                                        : launch_get_particles<float>(c, d_x, d_p));
+}
+
+pm_status pm_set_particles(pm_ctx* c, const double* d_x, const double* d_p, int32_t next_step) {
+  if (!c || !d_x || !d_p) return PM_ERR_ARG;
+  if (next_step < 0 || next_step > c->cfg.nsteps) return PM_ERR_ARG;
+  pm_status st = PM_DISPATCH(c, do_set_particles, c, d_x, d_p, next_step);
+  if (st) return st;
+  if (!c->ic_done) {
+    if (cudaMemsetAsync(c->ws + c->L.maps, 0, (size_t)c->cfg.n_zs * c->cfg.map_npix * c->cfg.map_npix * 8,
+                        c->stream))
+      return PM_ERR_CUDA;
+  }
+  c->ic_done = 1;
+  c->next_step = next_step;
+  c->last_stepped = next_step - 1;
+  c->projected = next_step - 2;
+  return PM_OK;
+}
+
+pm_status pm_get_forces(pm_ctx* c, double* d_f) {
+  if (!c || !d_f) return PM_ERR_ARG;
+  if (!c->ic_done) return PM_ERR_STATE;
+  return PM_DISPATCH(c, do_readout, c, c->L.fmesh, d_f);
+}
+
+pm_status pm_get_pgd(pm_ctx* c, double* d_s) {
+  if (!c || !d_s) return PM_ERR_ARG;
+  if (!c->ic_done || !c->pgd_valid) return PM_ERR_STATE;
+  return PM_DISPATCH(c, do_readout, c, c->L.smesh, d_s);
+}
+
+pm_status pm_fft_r2c(pm_ctx* c, const double* d_in, double* d_out) {
+  if (!c || !d_in || !d_out) return PM_ERR_ARG;
+  return PM_DISPATCH(c, do_fft, c, d_in, d_out);
+}
+
+pm_status pm_get_density(pm_ctx* c, double* d_rho) {
+  if (!c || !d_rho) return PM_ERR_ARG;
+  if (!c->ic_done) return PM_ERR_STATE;
+  return PM_DISPATCH(c, do_density, c, d_rho);
+}
+
+pm_status pm_sync_status(pm_ctx* c) {
+  if (!c) return PM_ERR_ARG;
+  return read_flags(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Launchers of the 3D FFT passes and of the fused spectral operators.
+#include "fft_impl.cuh"
+
+namespace pmlens {
+
+namespace {
+
+template <typename R, int N>
+struct Launch {
+  using C = typename CT<R>::T;
+  static size_t smem_x() { return (size_t)(N / 2 + RowTile<R, N>::ROWS * (N / 2 + 1)) * sizeof(C); }
+  static size_t smem_cols() { return (size_t)(N + N * ColTile<R, N>::W) * sizeof(C); }
+  static size_t smem_z() { return (size_t)(N + 2 * N * ColTile<R, N>::W) * sizeof(C); }
+  static int ntiles() { return (N / 2 + 1 + ColTile<R, N>::W - 1) / ColTile<R, N>::W; }
+
+  static void attrs() {
+    static bool done = false;
+    if (done) return;
+    cudaFuncSetAttribute(k_fft_x_r2c<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x());
+    cudaFuncSetAttribute(k_fft_x_c2r<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x());
+    cudaFuncSetAttribute(k_fft_cols<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols());
+    cudaFuncSetAttribute(k_fft_cols<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols());
+    cudaFuncSetAttribute(k_zpass_op<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z());
+    done = true;
+  }
+
+  static void x_fwd(const R* in, C* out, int P, cudaStream_t s) {
+    k_fft_x_r2c<R, N><<<(long long)N * N / RowTile<R, N>::ROWS, RowTile<R, N>::THREADS, smem_x(), s>>>(in, out, P);
+  }
+  static void x_inv(const C* in, R* out, int P, cudaStream_t s) {
+    k_fft_x_c2r<R, N><<<(long long)N * N / RowTile<R, N>::ROWS, RowTile<R, N>::THREADS, smem_x(), s>>>(in, out, P);
+  }
+  // y pass: planes = z (stride N*P), rows = y (stride P)
+  static void y(C* d, int P, bool inv, cudaStream_t s) {
+    dim3 g(ntiles(), N);
+    if (inv) k_fft_cols<R, N, true><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, (long long)N * P, P, N / 2 + 1);
+    else k_fft_cols<R, N, false><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, (long long)N * P, P, N / 2 + 1);
+  }
+  // z pass: planes = y (stride P), rows = z (stride N*P)
+  static void z(C* d, int P, bool inv, cudaStream_t s) {
+    dim3 g(ntiles(), N);
+    if (inv) k_fft_cols<R, N, true><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, P, (long long)N * P, N / 2 + 1);
+    else k_fft_cols<R, N, false><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, P, (long long)N * P, N / 2 + 1);
+  }
+  static void zop(const C* in, const OutPtrs& o, int nout, int P, const SpecParams& sp, cudaStream_t s) {
+    dim3 g(ntiles(), N);
+    k_zpass_op<R, N><<<g, ColTile<R, N>::THREADS, smem_z(), s>>>(in, o, nout, P, sp);
+  }
+
+  static cudaError_t r2c(const R* real, void* cplx, int P, cudaStream_t s) {
+    attrs();
+    C* c = reinterpret_cast<C*>(cplx);
+    x_fwd(real, c, P, s);
+    y(c, P, false, s);
+    z(c, P, false, s);
+    return cudaGetLastError();
+  }
+
+  static cudaError_t apply(const R* real_in, void* cbuf, void* const* ubufs, R* const* real_out, int nout, int P,
+                           const SpecParams& sp, cudaStream_t s) {
+    attrs();
+    C* c = reinterpret_cast<C*>(cbuf);
+    x_fwd(real_in, c, P, s);
+    y(c, P, false, s);
+    OutPtrs o;
+    for (int i = 0; i < 9; ++i) o.p[i] = i < nout ? ubufs[i] : nullptr;
+    zop(c, o, nout, P, sp, s);
+    for (int i = 0; i < nout; ++i) {
+      C* u = reinterpret_cast<C*>(ubufs[i]);
+      y(u, P, true, s);
+      x_inv(u, real_out[i], P, s);
+    }
+    return cudaGetLastError();
+  }
+};
+
+#define PM_FFT_DISPATCH(n, EXPR)                       \
+  switch (n) {                                         \
+    case 32: { using L = Launch<R, 32>; return EXPR; } \
+    case 64: { using L = Launch<R, 64>; return EXPR; } \
+    case 96: { using L = Launch<R, 96>; return EXPR; } \
+    case 128: { using L = Launch<R, 128>; return EXPR; } \
+    case 192: { using L = Launch<R, 192>; return EXPR; } \
+    case 256: { using L = Launch<R, 256>; return EXPR; } \
+    case 512: { using L = Launch<R, 512>; return EXPR; } \
+    case 1024: { using L = Launch<R, 1024>; return EXPR; } \
+    default: return cudaErrorInvalidValue;             \
+  }
+
+}  // namespace
+
+template <typename R>
+cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s) {
+  PM_FFT_DISPATCH(n, L::r2c(real, cplx, P, s));
+}
+
+template <typename R>
+cudaError_t spectral_apply(const R* real_in, void* cbuf, void* const* ubufs, R* const* real_out, int nout, int n,
+                           int P, const SpecParams& sp, cudaStream_t s) {
+  if (nout < 1 || nout > 9) return cudaErrorInvalidValue;
+  PM_FFT_DISPATCH(n, L::apply(real_in, cbuf, ubufs, real_out, nout, P, sp, s));
+}
+
+template cudaError_t fft3d_r2c<PM_REAL>(const PM_REAL*, void*, int, int, cudaStream_t);
+template cudaError_t spectral_apply<PM_REAL>(const PM_REAL*, void*, void* const*, PM_REAL* const*, int, int, int,
+                                              const SpecParams&, cudaStream_t);
+
+}  // namespace pmlens

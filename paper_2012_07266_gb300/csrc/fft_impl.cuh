@@ -1,0 +1,390 @@
+// Shared-memory Stockham FFT kernels for the 3D real-to-complex transforms of
+// the particle-mesh solver (force mesh and initial-condition lattice).
+//
+// Data layout: real meshes [z][y][x] (x fastest, no padding); complex
+// half-spectra [z][y][P] with P >= n/2 + 1 (row pitch rounded for alignment),
+// kx in 0..n/2, ky, kz in 0..n-1 (negative frequencies above n/2).
+//
+// Passes (all HBM-streaming, one read + one write of the mesh each):
+//  * x pass: each row of n reals is packed into n/2 complex values, FFT'd in
+//    shared memory and untangled into the n/2+1 half-spectrum (and back);
+//  * y / z passes: tiles of W adjacent kx columns (W*8 contiguous bytes per
+//    row, full 32-byte sectors) spanning the whole axis, FFT'd along the
+//    column in shared memory, written back in place;
+//  * the z pass of a force evaluation is fused with the Fourier-space
+//    operator: forward z FFT, multiply by each output's kernel (Poisson +
+//    gradient, PGD filter, LPT operators), inverse z FFT, store -- the
+//    spectrum itself never goes back to HBM.
+//
+// The 1D transform is a mixed-radix (8, 4, 2, 3) Stockham auto-sort FFT: each
+// stage reads the r inputs of a butterfly at stride n/r, applies twiddles
+// W_{Ns r}^{(j mod Ns) k}, a radix-r DFT in registers, and writes to
+// (j div Ns) Ns r + (j mod Ns) + k Ns, leaving the output in natural order.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pm_internal.h"
+
+namespace pmlens {
+
+template <typename R> struct CT;
+template <> struct CT<float> { using T = float2; };
+template <> struct CT<double> { using T = double2; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return C{a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return C{a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return C{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return C{a.x, -a.y}; }
+// multiply by -i (forward transforms) or +i (inverse transforms)
+template <bool INV, typename C> __device__ __forceinline__ C mul_mi(C a) {
+  return INV ? C{-a.y, a.x} : C{a.y, -a.x};
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C* v) {
+  const C a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  const C t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3), t3 = mul_mi<INV>(csub(v1, v3));
+  v0 = cadd(t0, t2);
+  v2 = csub(t0, t2);
+  v1 = cadd(t1, t3);
+  v3 = csub(t1, t3);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C* v) {
+  using R = decltype(C{}.x);
+  const R s = R(0.70710678118654752440);
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  // o1 *= W8, o2 *= W8^2, o3 *= W8^3 with W8 = exp(-/+ i pi / 4)
+  if (!INV) {
+    o1 = C{(o1.x + o1.y) * s, (o1.y - o1.x) * s};
+    o3 = C{(o3.y - o3.x) * s, -(o3.x + o3.y) * s};
+  } else {
+    o1 = C{(o1.x - o1.y) * s, (o1.x + o1.y) * s};
+    o3 = C{-(o3.x + o3.y) * s, (o3.x - o3.y) * s};
+  }
+  o2 = mul_mi<INV>(o2);
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1); v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2); v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3); v[7] = csub(e3, o3);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft3(C* v) {
+  using R = decltype(C{}.x);
+  const R h = R(0.86602540378443864676);  // sqrt(3)/2
+  const C s = cadd(v[1], v[2]), d = csub(v[1], v[2]);
+  const C m = C{v[0].x - R(0.5) * s.x, v[0].y - R(0.5) * s.y};
+  const C t = C{h * d.x, h * d.y};
+  v[0] = cadd(v[0], s);
+  if (!INV) {
+    v[1] = C{m.x + t.y, m.y - t.x};  // m - i t
+    v[2] = C{m.x - t.y, m.y + t.x};  // m + i t
+  } else {
+    v[1] = C{m.x - t.y, m.y + t.x};
+    v[2] = C{m.x + t.y, m.y - t.x};
+  }
+}
+
+template <int RAD, bool INV, typename C> __device__ __forceinline__ void dft(C* v) {
+  if constexpr (RAD == 2) dft2<INV>(v);
+  else if constexpr (RAD == 3) dft3<INV>(v);
+  else if constexpr (RAD == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else dft8<INV>(v);
+}
+
+template <int... Rs> struct Radices {};
+template <int N> struct Plan;
+template <> struct Plan<16> { static constexpr int V = 8; using Rad = Radices<8, 2>; };
+template <> struct Plan<32> { static constexpr int V = 8; using Rad = Radices<8, 4>; };
+template <> struct Plan<48> { static constexpr int V = 24; using Rad = Radices<8, 2, 3>; };
+template <> struct Plan<64> { static constexpr int V = 8; using Rad = Radices<8, 8>; };
+template <> struct Plan<96> { static constexpr int V = 24; using Rad = Radices<8, 4, 3>; };
+template <> struct Plan<128> { static constexpr int V = 8; using Rad = Radices<8, 8, 2>; };
+template <> struct Plan<192> { static constexpr int V = 24; using Rad = Radices<8, 8, 3>; };
+template <> struct Plan<256> { static constexpr int V = 8; using Rad = Radices<8, 8, 4>; };
+template <> struct Plan<512> { static constexpr int V = 8; using Rad = Radices<8, 8, 8>; };
+template <> struct Plan<1024> { static constexpr int V = 8; using Rad = Radices<8, 8, 8, 2>; };
+
+// One Stockham stage over a column of N elements at buf[row * rs + col * cs];
+// T = N / V threads per column, thread t handles V / RAD butterflies.
+template <typename C, int N, int V, int RAD, bool INV, int NS>
+__device__ __forceinline__ void stage(C* buf, int rs, int cs, int col, int t, const C* tw) {
+  constexpr int T = N / V;
+  constexpr int NB = V / RAD;
+  constexpr int NR = N / RAD;
+  constexpr int TSTR = N / (NS * RAD);
+  C v[NB][RAD];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = t + b * T;
+#pragma unroll
+    for (int k = 0; k < RAD; ++k) v[b][k] = buf[(j + k * NR) * rs + col * cs];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = t + b * T;
+    const int jm = j % NS;
+    if (NS > 1) {
+#pragma unroll
+      for (int k = 1; k < RAD; ++k) {
+        C w = tw[jm * k * TSTR];
+        if (INV) w.y = -w.y;
+        v[b][k] = cmul(v[b][k], w);
+      }
+    }
+    dft<RAD, INV>(v[b]);
+    const int base = (j - jm) * RAD + jm;
+#pragma unroll
+    for (int k = 0; k < RAD; ++k) buf[(base + k * NS) * rs + col * cs] = v[b][k];
+  }
+  __syncthreads();
+}
+
+template <typename C, int N, int V, bool INV, int NS, int RAD, int... Rest>
+__device__ __forceinline__ void run_stages(C* buf, int rs, int cs, int col, int t, const C* tw) {
+  stage<C, N, V, RAD, INV, NS>(buf, rs, cs, col, t, tw);
+  if constexpr (sizeof...(Rest) > 0) run_stages<C, N, V, INV, NS * RAD, Rest...>(buf, rs, cs, col, t, tw);
+}
+
+template <typename C, int N, bool INV, int... Rs>
+__device__ __forceinline__ void fft_column_impl(Radices<Rs...>, C* buf, int rs, int cs, int col, int t,
+                                                const C* tw) {
+  run_stages<C, N, Plan<N>::V, INV, 1, Rs...>(buf, rs, cs, col, t, tw);
+}
+
+// In-place FFT of one column of length N held in shared memory.
+template <typename C, int N, bool INV>
+__device__ __forceinline__ void fft_column(C* buf, int rs, int cs, int col, int t, const C* tw) {
+  fft_column_impl<C, N, INV>(typename Plan<N>::Rad{}, buf, rs, cs, col, t, tw);
+}
+
+// tw[m] = exp(-2 pi i m / N), m < N
+template <typename C, int N> __device__ __forceinline__ void make_twiddles(C* tw) {
+  using R = decltype(C{}.x);
+  for (int m = threadIdx.x; m < N; m += blockDim.x) {
+    R s, c;
+    if constexpr (sizeof(R) == 4) sincospif(-2.0f * (float)m / (float)N, &s, &c);
+    else sincospi(-2.0 * (double)m / (double)N, &s, &c);
+    tw[m] = C{c, s};
+  }
+}
+
+// ------------------------------------------------------------ tile widths
+template <typename R, int N> struct ColTile {
+  static constexpr int cap_smem = (sizeof(R) == 4 ? 8192 : 4096) / N;  // N*W*sizeof(C) <= 64 KB
+  static constexpr int cap_thr = 1024 * Plan<N>::V / N;
+  static constexpr int cap = cap_smem < cap_thr ? (cap_smem < 32 ? cap_smem : 32) : (cap_thr < 32 ? cap_thr : 32);
+  static constexpr int W = cap >= 32 ? 32 : cap >= 16 ? 16 : cap >= 8 ? 8 : cap >= 4 ? 4 : cap >= 2 ? 2 : 1;
+  static constexpr int THREADS = W * (N / Plan<N>::V);
+};
+
+template <typename R, int N> struct RowTile {  // x pass: rows of N reals, FFT length N/2
+  static constexpr int H = N / 2;
+  static constexpr int T = H / Plan<H>::V;
+  static constexpr int ROWS = (256 / T) > 0 ? (256 / T) : 1;
+  static constexpr int THREADS = ROWS * T;
+};
+
+// ---------------------------------------------------------------- kernels
+// x pass, forward: real rows -> half-spectrum rows
+template <typename R, int N>
+__global__ void __launch_bounds__(RowTile<R, N>::THREADS)
+k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P) {
+  using C = typename CT<R>::T;
+  constexpr int H = N / 2, ROWS = RowTile<R, N>::ROWS, T = RowTile<R, N>::T, LD = H + 1;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf = tw + H;
+  make_twiddles<C, H>(tw);
+  const long long row0 = (long long)blockIdx.x * ROWS;
+  const C* inc = reinterpret_cast<const C*>(in);
+  for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
+    const int h = e / H, m = e - h * H;
+    buf[h * LD + m] = inc[(row0 + h) * H + m];
+  }
+  __syncthreads();
+  const int h = threadIdx.x / T, t = threadIdx.x - h * T;
+  fft_column<C, H, false>(buf, 1, LD, h, t, tw);
+  for (int e = threadIdx.x; e < ROWS * (H + 1); e += blockDim.x) {
+    const int hh = e / (H + 1), k = e - hh * (H + 1);
+    const C zk = buf[hh * LD + (k % H)];
+    const C zm = cconj(buf[hh * LD + ((H - k) % H)]);
+    const C ev = C{R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y)};
+    const C od = C{R(0.5) * (zk.y - zm.y), -R(0.5) * (zk.x - zm.x)};  // (zk - zm) / (2i)
+    R s, c;
+    if constexpr (sizeof(R) == 4) sincospif(-2.0f * (float)k / (float)N, &s, &c);
+    else sincospi(-2.0 * (double)k / (double)N, &s, &c);
+    out[(row0 + hh) * P + k] = cadd(ev, cmul(C{c, s}, od));
+  }
+}
+
+// x pass, inverse: half-spectrum rows -> real rows (unnormalised: n * IDFT)
+template <typename R, int N>
+__global__ void __launch_bounds__(RowTile<R, N>::THREADS)
+k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P) {
+  using C = typename CT<R>::T;
+  constexpr int H = N / 2, ROWS = RowTile<R, N>::ROWS, T = RowTile<R, N>::T, LD = H + 1;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf = tw + H;
+  make_twiddles<C, H>(tw);
+  const long long row0 = (long long)blockIdx.x * ROWS;
+  for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
+    const int h = e / H, k = e - h * H;
+    const C xk = in[(row0 + h) * P + k];
+    const C xm = cconj(in[(row0 + h) * P + (H - k)]);
+    const C ev = cadd(xk, xm);
+    R s, c;
+    if constexpr (sizeof(R) == 4) sincospif(2.0f * (float)k / (float)N, &s, &c);
+    else sincospi(2.0 * (double)k / (double)N, &s, &c);
+    const C od = cmul(C{c, s}, csub(xk, xm));
+    buf[h * LD + k] = C{ev.x - od.y, ev.y + od.x};  // ev + i od
+  }
+  __syncthreads();
+  const int h = threadIdx.x / T, t = threadIdx.x - h * T;
+  fft_column<C, H, true>(buf, 1, LD, h, t, tw);
+  C* outc = reinterpret_cast<C*>(out);
+  for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
+    const int hh = e / H, m = e - hh * H;
+    outc[(row0 + hh) * H + m] = buf[hh * LD + m];
+  }
+}
+
+// y or z pass in place: column tiles of W kx values over a full axis.
+template <typename R, int N, bool INV>
+__global__ void __launch_bounds__(ColTile<R, N>::THREADS)
+k_fft_cols(typename CT<R>::T* __restrict__ data, long long plane_stride, long long row_stride, int ncols) {
+  using C = typename CT<R>::T;
+  constexpr int W = ColTile<R, N>::W;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf = tw + N;
+  make_twiddles<C, N>(tw);
+  const int kx0 = blockIdx.x * W;
+  C* base = data + (long long)blockIdx.y * plane_stride + kx0;
+  const int nv = min(W, ncols - kx0);
+  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+    const int row = e / W, c = e - row * W;
+    buf[e] = c < nv ? base[row * row_stride + c] : C{0, 0};
+  }
+  __syncthreads();
+  const int col = threadIdx.x % W, t = threadIdx.x / W;
+  fft_column<C, N, INV>(buf, W, 1, col, t, tw);
+  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+    const int row = e / W, c = e - row * W;
+    if (c < nv) base[row * row_stride + c] = buf[e];
+  }
+}
+
+struct OutPtrs { void* p[9]; };
+
+// Fourier-space operator for output o at integer frequencies (fx, fy, fz).
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T spec_mult(const SpecParams& sp, int o, int ix, int iy, int iz,
+                                                       int n, typename CT<R>::T a) {
+  using C = typename CT<R>::T;
+  const int h = n / 2;
+  const int fx = ix <= h ? ix : ix - n, fy = iy <= h ? iy : iy - n, fz = iz <= h ? iz : iz - n;
+  const R kf = (R)sp.kf;
+  const R kx = kf * fx, ky = kf * fy, kz = kf * fz;
+  const R k2 = kx * kx + ky * ky + kz * kz;
+  const R inv = k2 > R(0) ? R(1) / k2 : R(0);
+  // odd factors vanish on their axis' Nyquist plane
+  const R ox = ix == h ? R(0) : kx, oy = iy == h ? R(0) : ky, oz = iz == h ? R(0) : kz;
+  R re = 0, im = 0;  // multiplier = re + i im
+  switch (sp.op) {
+    case OP_FORCE:
+    case OP_FORCE_PGD: {
+      const R odd = o % 3 == 0 ? ox : (o % 3 == 1 ? oy : oz);
+      R s = (R)sp.scale;
+      if (o >= 3) {
+        const R kk = sqrt(k2);
+        const R filt = k2 > R(0) ? exp(-(R)(sp.kl * sp.kl) * inv) * exp(-pow(kk / (R)sp.ks, (R)sp.nexp)) : R(0);
+        s = (R)sp.pgd_scale * filt;
+      }
+      im = s * odd * inv;
+      break;
+    }
+    case OP_LPT1:
+    case OP_LPT2_DERIV: {
+      const R amp = (R)sp.sqrtp[fx * fx + fy * fy + fz * fz] * (R)sp.scale;
+      if (o < 3) {
+        const R odd = o == 0 ? ox : (o == 1 ? oy : oz);
+        im = amp * odd * inv;
+      } else {
+        // Psi1_{i,j} = -k_i k_j / k^2 delta: (0,0),(1,1),(2,2),(0,1),(0,2),(1,2)
+        const int q = o - 3;
+        R f;
+        if (q == 0) f = kx * kx;
+        else if (q == 1) f = ky * ky;
+        else if (q == 2) f = kz * kz;
+        else if (q == 3) f = ox * oy;
+        else if (q == 4) f = ox * oz;
+        else f = oy * oz;
+        re = -amp * f * inv;
+      }
+      break;
+    }
+    case OP_GRAD_NEG: {
+      const R odd = o == 0 ? ox : (o == 1 ? oy : oz);
+      im = -(R)sp.scale * odd * inv;
+      break;
+    }
+    default:
+      re = (R)sp.scale;
+  }
+  return C{re * a.x - im * a.y, re * a.y + im * a.x};
+}
+
+// fused z pass: forward z FFT, per-output multiplier, inverse z FFT, store.
+template <typename R, int N>
+__global__ void __launch_bounds__(ColTile<R, N>::THREADS)
+k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int P, SpecParams sp) {
+  using C = typename CT<R>::T;
+  constexpr int W = ColTile<R, N>::W;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* A = tw + N;
+  C* B = A + N * W;
+  make_twiddles<C, N>(tw);
+  const int ncols = N / 2 + 1;
+  const int kx0 = blockIdx.x * W;
+  const int iy = blockIdx.y;
+  const long long plane = (long long)iy * P + kx0;
+  const long long rstride = (long long)N * P;
+  const int nv = min(W, ncols - kx0);
+  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+    const int row = e / W, c = e - row * W;
+    A[e] = c < nv ? in[plane + row * rstride + c] : C{0, 0};
+  }
+  __syncthreads();
+  const int col = threadIdx.x % W, t = threadIdx.x / W;
+  fft_column<C, N, false>(A, W, 1, col, t, tw);
+  for (int o = 0; o < nout; ++o) {
+    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+      const int row = e / W, c = e - row * W;
+      B[e] = spec_mult<R>(sp, o, kx0 + c, iy, row, N, A[e]);
+    }
+    __syncthreads();
+    fft_column<C, N, true>(B, W, 1, col, t, tw);
+    C* dst = reinterpret_cast<C*>(outs.p[o]) + plane;
+    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+      const int row = e / W, c = e - row * W;
+      if (c < nv) dst[row * rstride + c] = B[e];
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace pmlens

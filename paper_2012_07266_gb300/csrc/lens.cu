@@ -1,0 +1,217 @@
+// Born lightcone projection (Eq. conv) with box replication/rotation and the
+// sub-evolution scheme (Sec. 3), and the final mean-density subtraction.
+//
+// One thread per particle, replicas looped in registers: the particle is read
+// once (cell, fraction, momentum, optional PGD displacement gathered from the
+// PGD meshes) and tested against every replica of the shell.  Geometry runs in
+// the path's precision (FP32 fast path: positions in Mpc/h to ~1e-7 relative),
+// the lensing weights and the map accumulation always in FP64.
+#include <cmath>
+
+#include "pm_internal.h"
+
+namespace pmlens {
+
+namespace {
+
+template <typename R>
+struct LensArgs {
+  const uint32_t* cell;
+  const R *fx, *fy, *fz, *px, *py, *pz;
+  const R *S0, *S1, *S2;  // PGD displacement meshes (cells), or null
+  long long np;
+  int M;
+  double cell_len;
+  double chi_lo2, chi_hi2;
+  double fov_half, inv_dtheta;
+  int npix, nzs, sub;
+  double chi_s[PM_MAX_ZS];
+  double wpref;            // (3/2) Om (H0/c)^2 V_p / Omega_pix
+  double d1_next, inv_gp_half;
+  double tab_hinv;
+  int tab_n;
+  const double* tab_d1;    // D1(a(chi)) on a uniform chi grid
+  const double* tab_inva;  // 1 / a(chi)
+  double* maps;
+  int* flag;
+  int nrep;
+  Replica rep[kMaxReplicas];
+};
+
+struct MeanTerms { double v[PM_MAX_ZS]; };
+
+__device__ __forceinline__ double interp(const double* __restrict__ t, int n, double hinv, double x) {
+  double u = x * hinv;
+  int k = (int)u;
+  if (k < 0) k = 0;
+  if (k > n - 2) k = n - 2;
+  const double f = u - k;
+  return t[k] * (1.0 - f) + t[k + 1] * f;
+}
+
+template <typename R>
+__device__ __forceinline__ R gather3(const R* __restrict__ m, int M, int ix, int iy, int iz, R fx, R fy, R fz) {
+  const int ix1 = ix + 1 == M ? 0 : ix + 1, iy1 = iy + 1 == M ? 0 : iy + 1, iz1 = iz + 1 == M ? 0 : iz + 1;
+  const long long r00 = ((long long)iz * M + iy) * M, r01 = ((long long)iz * M + iy1) * M;
+  const long long r10 = ((long long)iz1 * M + iy) * M, r11 = ((long long)iz1 * M + iy1) * M;
+  const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
+  const R a = gx * m[r00 + ix] + fx * m[r00 + ix1];
+  const R b = gx * m[r01 + ix] + fx * m[r01 + ix1];
+  const R d = gx * m[r10 + ix] + fx * m[r10 + ix1];
+  const R e = gx * m[r11 + ix] + fx * m[r11 + ix1];
+  return gz * (gy * a + fy * b) + fz * (gy * d + fy * e);
+}
+
+// Geometry runs in the path's precision R (FP32 fast path, FP64 plain path).
+template <typename R>
+__global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
+  const R cell_len = (R)A.cell_len, lo2 = (R)A.chi_lo2, hi2 = (R)A.chi_hi2;
+  const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.np;
+       j += (long long)gridDim.x * blockDim.x) {
+    const uint32_t c = A.cell[j];
+    const int ci[3] = {(int)(c & 1023u), (int)((c >> 10) & 1023u), (int)(c >> 20)};
+    const R cf[3] = {A.fx[j], A.fy[j], A.fz[j]};
+    const R cp[3] = {A.px[j], A.py[j], A.pz[j]};
+    R cs[3] = {R(0), R(0), R(0)};
+    if (A.S0) {
+      cs[0] = gather3(A.S0, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
+      cs[1] = gather3(A.S1, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
+      cs[2] = gather3(A.S2, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
+    }
+    for (int q = 0; q < A.nrep; ++q) {
+      const Replica rp = A.rep[q];
+      R r[3], pr[3], sr[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int ax = rp.perm[d];
+        int i = ci[ax];
+        R f = cf[ax];
+        R sg = R(1);
+        if (rp.flip >> d & 1) {
+          if (f > R(0)) { i = A.M - 1 - i; f = R(1) - f; }
+          else { i = i == 0 ? 0 : A.M - i; }
+          sg = R(-1);
+        }
+        i += rp.shift[d];
+        if (i >= A.M) i -= A.M;
+        r[d] = ((R)(i + rp.n[d] * A.M) + f) * cell_len;
+        pr[d] = sg * cp[ax];
+        sr[d] = sg * cs[ax];
+      }
+      const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) continue;
+      if (A.sub) {
+        const double t = interp(A.tab_d1, A.tab_n, A.tab_hinv, (double)sqrt(chi2));
+        const R dt = (R)((t - A.d1_next) * A.inv_gp_half) * cell_len;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) r[d] += pr[d] * dt;
+      }
+      if (A.S0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) r[d] += sr[d] * cell_len;
+      }
+      if (!(r[2] > R(0))) continue;
+      const R chic = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+      const R inz = R(1) / r[2];
+      const R u = (r[0] * inz + fov_half) * inv_dth - R(0.5);
+      const R v = (r[1] * inz + fov_half) * inv_dth - R(0.5);
+      if (!isfinite(u) || !isfinite(v) || !isfinite(chic)) {
+        atomicOr(A.flag, 1);
+        continue;
+      }
+      if (u < R(-1) || v < R(-1) || u >= (R)A.npix || v >= (R)A.npix) continue;
+      const R fu0 = floor(u), fv0 = floor(v);
+      const int iu = (int)fu0, iv = (int)fv0;
+      const R fu = u - fu0, fv = v - fv0;
+      const double cd = (double)chic;
+      const double inva = interp(A.tab_inva, A.tab_n, A.tab_hinv, cd);
+      const R cw[4] = {(R(1) - fu) * (R(1) - fv), fu * (R(1) - fv), (R(1) - fu) * fv, fu * fv};
+      for (int s = 0; s < A.nzs; ++s) {
+        const double cs_ = A.chi_s[s];
+        if (!(cd < cs_)) continue;
+        const double w = A.wpref * (cs_ - cd) / (cs_ * cd) * inva;
+        double* m = A.maps + (long long)s * A.npix * A.npix;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int jx = iu + (k & 1), jy = iv + (k >> 1);
+          if (jx >= 0 && jx < A.npix && jy >= 0 && jy < A.npix)
+            atomicAdd(m + (long long)jy * A.npix + jx, w * (double)cw[k]);
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_kappa_finalize(const double* __restrict__ maps, double* __restrict__ out, long long npix2, int nzs,
+                                 MeanTerms mt, int* flag) {
+  const long long n = npix2 * nzs;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const double v = maps[j] - mt.v[j / npix2];
+    if (!isfinite(v)) atomicOr(flag, 2);
+    out[j] = v;
+  }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
+  LensArgs<R> A;
+  A.cell = reinterpret_cast<const uint32_t*>(c->ws + c->L.cell);
+  const R* f = reinterpret_cast<const R*>(c->ws + c->L.frac);
+  const R* p = reinterpret_cast<const R*>(c->ws + c->L.mom);
+  A.fx = f; A.fy = f + c->np; A.fz = f + 2 * c->np;
+  A.px = p; A.py = p + c->np; A.pz = p + 2 * c->np;
+  if (use_pgd) {
+    const R* S = reinterpret_cast<const R*>(c->ws + c->L.smesh);
+    A.S0 = S; A.S1 = S + c->mesh_elems; A.S2 = S + 2 * c->mesh_elems;
+  } else {
+    A.S0 = A.S1 = A.S2 = nullptr;
+  }
+  A.np = c->np;
+  A.M = c->M;
+  A.cell_len = c->cfg.box / c->M;
+  A.chi_lo2 = sh.chi_lo2;
+  A.chi_hi2 = sh.chi_hi2;
+  const double fov = c->cfg.map_fov_deg * M_PI / 180.0;
+  const double dth = fov / c->cfg.map_npix;
+  A.fov_half = 0.5 * fov;
+  A.inv_dtheta = 1.0 / dth;
+  A.npix = c->cfg.map_npix;
+  A.nzs = c->cfg.n_zs;
+  for (int s = 0; s < PM_MAX_ZS; ++s) A.chi_s[s] = s < c->cfg.n_zs ? c->chi_s[s] : 0.0;
+  const double vp = std::pow(c->cfg.box / c->nc, 3.0);
+  A.wpref = 1.5 * c->cfg.omega_m / (kCoverH0 * kCoverH0) * vp / (dth * dth);
+  A.d1_next = sh.d1_next;
+  A.inv_gp_half = 1.0 / sh.gp_half;
+  A.sub = c->cfg.sub_evolution;
+  A.tab_hinv = 1.0 / c->chi_tab_h;
+  A.tab_n = kChiTab;
+  A.tab_d1 = reinterpret_cast<const double*>(c->ws + c->L.tab_d1);
+  A.tab_inva = reinterpret_cast<const double*>(c->ws + c->L.tab_inva);
+  A.maps = reinterpret_cast<double*>(c->ws + c->L.maps);
+  A.flag = flags_ptr(c);
+  A.nrep = sh.nrep;
+  for (int q = 0; q < sh.nrep; ++q) A.rep[q] = sh.rep[q];
+  long long blocks = (c->np + 255) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  k_lens<R><<<(int)blocks, 256, 0, c->stream>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kappa_finalize(pm_ctx* c, double* out) {
+  const long long npix2 = (long long)c->cfg.map_npix * c->cfg.map_npix;
+  MeanTerms mt;
+  for (int s = 0; s < PM_MAX_ZS; ++s) mt.v[s] = s < c->cfg.n_zs ? c->mean_term[s] : 0.0;
+  long long blocks = (npix2 * c->cfg.n_zs + 255) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  k_kappa_finalize<<<(int)blocks, 256, 0, c->stream>>>(reinterpret_cast<const double*>(c->ws + c->L.maps), out,
+                                                       npix2, c->cfg.n_zs, mt, flags_ptr(c));
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_lens<float>(pm_ctx*, const LensShell&, int);
+template cudaError_t launch_lens<double>(pm_ctx*, const LensShell&, int);
+
+}  // namespace pmlens

@@ -1,0 +1,324 @@
+// Particle kernels: LPT initial positions, cloud-in-cell paint, the fused
+// kick + drift + paint of a FastPM step, CIC readout, state transfer.
+//
+// Particle state (structure of arrays, HBM resident): a packed uint32 cell
+// index (ix | iy << 10 | iz << 20, force-mesh cells, mesh <= 1024) and the
+// in-cell fraction f in [0, 1) per axis, so that the position is (i + f) cells;
+// momentum in cell units.  Positions keep ~2^-24 cell precision everywhere in
+// the box with FP32 fractions.
+#include <cmath>
+
+#include "pm_internal.h"
+
+namespace pmlens {
+
+namespace {
+
+__device__ __forceinline__ void unpack(uint32_t c, int& ix, int& iy, int& iz) {
+  ix = c & 1023u;
+  iy = (c >> 10) & 1023u;
+  iz = c >> 20;
+}
+__device__ __forceinline__ uint32_t pack(int ix, int iy, int iz) {
+  return (uint32_t)ix | ((uint32_t)iy << 10) | ((uint32_t)iz << 20);
+}
+__device__ __forceinline__ int wrapi(long long i, int M) {
+  long long r = i % M;
+  return (int)(r < 0 ? r + M : r);
+}
+
+// split a coordinate in cells into (wrapped integer cell, fraction in [0,1))
+template <typename R>
+__device__ __forceinline__ void split_cells(double X, int M, int& i, R& f) {
+  const double fl = floor(X);
+  R fr = (R)(X - fl);
+  long long ii = (long long)fl;
+  if (fr >= R(1)) { fr = R(0); ii += 1; }
+  i = wrapi(ii, M);
+  f = fr;
+}
+
+struct Corners {
+  long long r00, r01, r10, r11;  // row offsets (z, y) of the 4 x-rows
+  int x0, x1;
+};
+
+__device__ __forceinline__ Corners corners(int M, int ix, int iy, int iz) {
+  const int ix1 = ix + 1 == M ? 0 : ix + 1;
+  const int iy1 = iy + 1 == M ? 0 : iy + 1;
+  const int iz1 = iz + 1 == M ? 0 : iz + 1;
+  Corners c;
+  c.r00 = ((long long)iz * M + iy) * M;
+  c.r01 = ((long long)iz * M + iy1) * M;
+  c.r10 = ((long long)iz1 * M + iy) * M;
+  c.r11 = ((long long)iz1 * M + iy1) * M;
+  c.x0 = ix;
+  c.x1 = ix1;
+  return c;
+}
+
+template <typename R>
+__device__ __forceinline__ R gather(const R* __restrict__ m, const Corners& c, R fx, R fy, R fz) {
+  const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
+  const R a = gx * __ldg(m + c.r00 + c.x0) + fx * __ldg(m + c.r00 + c.x1);
+  const R b = gx * __ldg(m + c.r01 + c.x0) + fx * __ldg(m + c.r01 + c.x1);
+  const R d = gx * __ldg(m + c.r10 + c.x0) + fx * __ldg(m + c.r10 + c.x1);
+  const R e = gx * __ldg(m + c.r11 + c.x0) + fx * __ldg(m + c.r11 + c.x1);
+  return gz * (gy * a + fy * b) + fz * (gy * d + fy * e);
+}
+
+template <typename R>
+__device__ __forceinline__ void scatter(R* __restrict__ m, const Corners& c, R fx, R fy, R fz, R w) {
+  const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
+  const R w00 = w * gz * gy, w01 = w * gz * fy, w10 = w * fz * gy, w11 = w * fz * fy;
+  atomicAdd(m + c.r00 + c.x0, w00 * gx);
+  atomicAdd(m + c.r00 + c.x1, w00 * fx);
+  atomicAdd(m + c.r01 + c.x0, w01 * gx);
+  atomicAdd(m + c.r01 + c.x1, w01 * fx);
+  atomicAdd(m + c.r10 + c.x0, w10 * gx);
+  atomicAdd(m + c.r10 + c.x1, w10 * fx);
+  atomicAdd(m + c.r11 + c.x0, w11 * gx);
+  atomicAdd(m + c.r11 + c.x1, w11 * fx);
+}
+
+template <typename R>
+struct PState {
+  uint32_t* cell;
+  R *fx, *fy, *fz, *px, *py, *pz;
+};
+
+template <typename R>
+PState<R> pstate(pm_ctx* c) {
+  PState<R> s;
+  s.cell = reinterpret_cast<uint32_t*>(c->ws + c->L.cell);
+  R* f = reinterpret_cast<R*>(c->ws + c->L.frac);
+  R* p = reinterpret_cast<R*>(c->ws + c->L.mom);
+  s.fx = f; s.fy = f + c->np; s.fz = f + 2 * c->np;
+  s.px = p; s.py = p + c->np; s.pz = p + 2 * c->np;
+  return s;
+}
+
+inline int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  const long long cap = 152LL * 16;
+  return (int)(b < cap ? b : cap);
+}
+
+// ------------------------------------------------------------------ kernels
+template <typename R>
+__global__ void k_ic_particles(PState<R> s, const R* __restrict__ p1x, const R* __restrict__ p1y,
+                               const R* __restrict__ p1z, const R* __restrict__ p2x, const R* __restrict__ p2y,
+                               const R* __restrict__ p2z, int nc, int M, double cell_per_len, double d1,
+                               double d2, double gp1, double gp2, long long np) {
+  const double lat = (double)M / (double)nc;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+    const int jx = (int)(j % nc), jy = (int)((j / nc) % nc), jz = (int)(j / ((long long)nc * nc));
+    double sx = p1x[j], sy = p1y[j], sz = p1z[j];
+    double tx = 0, ty = 0, tz = 0;
+    if (p2x) { tx = p2x[j]; ty = p2y[j]; tz = p2z[j]; }
+    int ix, iy, iz;
+    R fx, fy, fz;
+    split_cells<R>(jx * lat + 0.5 + (d1 * sx + d2 * tx) * cell_per_len, M, ix, fx);
+    split_cells<R>(jy * lat + 0.5 + (d1 * sy + d2 * ty) * cell_per_len, M, iy, fy);
+    split_cells<R>(jz * lat + 0.5 + (d1 * sz + d2 * tz) * cell_per_len, M, iz, fz);
+    s.cell[j] = pack(ix, iy, iz);
+    s.fx[j] = fx; s.fy[j] = fy; s.fz[j] = fz;
+    s.px[j] = (R)((gp1 * sx + gp2 * tx) * cell_per_len);
+    s.py[j] = (R)((gp1 * sy + gp2 * ty) * cell_per_len);
+    s.pz[j] = (R)((gp1 * sz + gp2 * tz) * cell_per_len);
+  }
+}
+
+template <typename R>
+__global__ void k_paint(PState<R> s, R* __restrict__ rho, int M, R mass, long long np) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    unpack(s.cell[j], ix, iy, iz);
+    scatter(rho, corners(M, ix, iy, iz), s.fx[j], s.fy[j], s.fz[j], mass);
+  }
+}
+
+// kick with the force at the current positions, drift, paint the new position
+template <typename R>
+__global__ void k_kdk_paint(PState<R> s, const R* __restrict__ F0, const R* __restrict__ F1,
+                            const R* __restrict__ F2, R* __restrict__ rho, int M, R ckick, R cdrift, R mass,
+                            long long np) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    unpack(s.cell[j], ix, iy, iz);
+    R fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
+    const Corners c = corners(M, ix, iy, iz);
+    const R px = s.px[j] + ckick * gather(F0, c, fx, fy, fz);
+    const R py = s.py[j] + ckick * gather(F1, c, fx, fy, fz);
+    const R pz = s.pz[j] + ckick * gather(F2, c, fx, fy, fz);
+    s.px[j] = px; s.py[j] = py; s.pz[j] = pz;
+    // drift in cell units; carry the integer part into the cell index
+    R nx = fx + px * cdrift, ny = fy + py * cdrift, nz = fz + pz * cdrift;
+    R cx = floor(nx), cy = floor(ny), cz = floor(nz);
+    nx -= cx; ny -= cy; nz -= cz;
+    if (nx >= R(1)) { nx -= R(1); cx += R(1); }
+    if (ny >= R(1)) { ny -= R(1); cy += R(1); }
+    if (nz >= R(1)) { nz -= R(1); cz += R(1); }
+    ix = wrapi((long long)ix + (long long)cx, M);
+    iy = wrapi((long long)iy + (long long)cy, M);
+    iz = wrapi((long long)iz + (long long)cz, M);
+    s.cell[j] = pack(ix, iy, iz);
+    s.fx[j] = nx; s.fy[j] = ny; s.fz[j] = nz;
+    scatter(rho, corners(M, ix, iy, iz), nx, ny, nz, mass);
+  }
+}
+
+template <typename R>
+__global__ void k_readout(PState<R> s, const R* __restrict__ m0, const R* __restrict__ m1,
+                          const R* __restrict__ m2, int M, double scale, double* __restrict__ out, long long np) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    unpack(s.cell[j], ix, iy, iz);
+    const Corners c = corners(M, ix, iy, iz);
+    const R fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
+    out[3 * j + 0] = scale * (double)gather(m0, c, fx, fy, fz);
+    out[3 * j + 1] = scale * (double)gather(m1, c, fx, fy, fz);
+    out[3 * j + 2] = scale * (double)gather(m2, c, fx, fy, fz);
+  }
+}
+
+template <typename R>
+__global__ void k_set_particles(PState<R> s, const double* __restrict__ x, const double* __restrict__ p, int M,
+                                double cell_per_len, long long np) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    R fx, fy, fz;
+    split_cells<R>(x[3 * j + 0] * cell_per_len, M, ix, fx);
+    split_cells<R>(x[3 * j + 1] * cell_per_len, M, iy, fy);
+    split_cells<R>(x[3 * j + 2] * cell_per_len, M, iz, fz);
+    s.cell[j] = pack(ix, iy, iz);
+    s.fx[j] = fx; s.fy[j] = fy; s.fz[j] = fz;
+    s.px[j] = (R)(p[3 * j + 0] * cell_per_len);
+    s.py[j] = (R)(p[3 * j + 1] * cell_per_len);
+    s.pz[j] = (R)(p[3 * j + 2] * cell_per_len);
+  }
+}
+
+template <typename R>
+__global__ void k_get_particles(PState<R> s, double* __restrict__ x, double* __restrict__ p, double len_per_cell,
+                                long long np) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+    int ix, iy, iz;
+    unpack(s.cell[j], ix, iy, iz);
+    if (x) {
+      x[3 * j + 0] = ((double)ix + (double)s.fx[j]) * len_per_cell;
+      x[3 * j + 1] = ((double)iy + (double)s.fy[j]) * len_per_cell;
+      x[3 * j + 2] = ((double)iz + (double)s.fz[j]) * len_per_cell;
+    }
+    if (p) {
+      p[3 * j + 0] = (double)s.px[j] * len_per_cell;
+      p[3 * j + 1] = (double)s.py[j] * len_per_cell;
+      p[3 * j + 2] = (double)s.pz[j] * len_per_cell;
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_lpt2_source(const R* __restrict__ d00, const R* __restrict__ d11, const R* __restrict__ d22,
+                              const R* __restrict__ d01, const R* __restrict__ d02, const R* __restrict__ d12,
+                              R* __restrict__ src, long long n) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const R a = d00[j], b = d11[j], c = d22[j], e = d01[j], f = d02[j], g = d12[j];
+    src[j] = a * b + a * c + b * c - e * e - f * f - g * g;
+  }
+}
+
+template <typename R>
+__global__ void k_convert_in(const double* __restrict__ in, R* __restrict__ out, long long n) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    out[j] = (R)in[j];
+}
+
+template <typename R>
+__global__ void k_convert_out(const R* __restrict__ in, double* __restrict__ out, long long n, double scale) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    out[j] = scale * (double)in[j];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+template <typename R>
+cudaError_t launch_ic_particles(pm_ctx* c, R* const* psi1, R* const* psi2, double d1, double d2, double gp1,
+                                double gp2) {
+  const double cpl = c->M / c->cfg.box;
+  k_ic_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(
+      pstate<R>(c), psi1[0], psi1[1], psi1[2], psi2 ? psi2[0] : nullptr, psi2 ? psi2[1] : nullptr,
+      psi2 ? psi2[2] : nullptr, c->nc, c->M, cpl, d1, d2, gp1, gp2, c->np);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_paint(pm_ctx* c, R* rho) {
+  const double mass = std::pow((double)c->M / c->nc, 3.0);
+  k_paint<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), rho, c->M, (R)mass, c->np);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_kdk_paint(pm_ctx* c, R* rho, double ckick, double cdrift) {
+  const double mass = std::pow((double)c->M / c->nc, 3.0);
+  R* F = reinterpret_cast<R*>(c->ws + c->L.fmesh);
+  k_kdk_paint<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), F, F + c->mesh_elems,
+                                                               F + 2 * c->mesh_elems, rho, c->M, (R)ckick,
+                                                               (R)cdrift, (R)mass, c->np);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_readout(pm_ctx* c, R* const* meshes, double scale, double* out) {
+  k_readout<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), meshes[0], meshes[1], meshes[2], c->M,
+                                                             scale, out, c->np);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_set_particles(pm_ctx* c, const double* x, const double* p) {
+  k_set_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), x, p, c->M, c->M / c->cfg.box,
+                                                                   c->np);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_get_particles(pm_ctx* c, double* x, double* p) {
+  k_get_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), x, p, c->cfg.box / c->M, c->np);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_lpt2_source(pm_ctx* c, R* const* d, R* src, long long n) {
+  k_lpt2_source<R><<<grid_for(n, 256), 256, 0, c->stream>>>(d[0], d[1], d[2], d[3], d[4], d[5], src, n);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_convert_in(const double* in, R* out, long long n, cudaStream_t s) {
+  k_convert_in<R><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_convert_out(const R* in, double* out, long long n, double scale, cudaStream_t s) {
+  k_convert_out<R><<<grid_for(n, 256), 256, 0, s>>>(in, out, n, scale);
+  return cudaGetLastError();
+}
+
+#define PM_INST(R)                                                                                        \
+  template cudaError_t launch_ic_particles<R>(pm_ctx*, R* const*, R* const*, double, double, double, double); \
+  template cudaError_t launch_paint<R>(pm_ctx*, R*);                                                      \
+  template cudaError_t launch_kdk_paint<R>(pm_ctx*, R*, double, double);                                  \
+  template cudaError_t launch_readout<R>(pm_ctx*, R* const*, double, double*);                            \
+  template cudaError_t launch_set_particles<R>(pm_ctx*, const double*, const double*);                    \
+  template cudaError_t launch_get_particles<R>(pm_ctx*, double*, double*);                                \
+  template cudaError_t launch_lpt2_source<R>(pm_ctx*, R* const*, R*, long long);                          \
+  template cudaError_t launch_convert_in<R>(const double*, R*, long long, cudaStream_t);                   \
+  template cudaError_t launch_convert_out<R>(const R*, double*, long long, double, cudaStream_t);
+PM_INST(float)
+PM_INST(double)
+
+}  // namespace pmlens

@@ -1,0 +1,159 @@
+// Internal declarations of the PM lensing library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/pm.h"
+
+namespace pmlens {
+
+constexpr double kCoverH0 = 2997.92458;  // c / H0 in Mpc/h
+constexpr int kMaxReplicas = 96;         // replicas per lens launch (more -> several launches)
+constexpr int kChiTab = 16384;           // entries of the chi -> (D1, 1/a) tables
+
+// ---------------------------------------------------------------- cosmology
+// FP64 background on the host: linear growth by RK4 in ln a with cubic
+// Hermite interpolation, comoving distance, Eisenstein-Hu linear power.
+struct Cosmo {
+  double om, s8, h, ns, ob, tcmb;
+  // tables on a uniform ln a grid
+  double lna0, dlna;
+  int n;
+  std::vector<double> d1, d1d, d2, d2d, chi;  // D1, dD1/dlna, D2, dD2/dlna, chi
+  double pk_norm;
+
+  void init(double omega_m, double sigma8, double hh, double n_s, double omega_b, double t_cmb);
+  double E(double a) const;
+  double dlnE_dlna(double a) const;
+  void state(double a, double* D1, double* dD1, double* D2, double* dD2) const;
+  double D1(double a) const;
+  double D2(double a) const;
+  double gp(double a) const;   // a^3 E dD1/da
+  double gp2(double a) const;  // a^3 E dD2/da
+  double gf(double a) const;   // a^2 E dgp/da
+  double chi_a(double a) const;
+  double a_of_chi(double c) const;
+  double transfer(double k_hmpc) const;  // Eisenstein & Hu (1998) with BAO
+  double pk(double k_hmpc) const;        // sigma8-normalised linear P(k), z = 0
+};
+
+// per-replica transform, packed for kernel parameters
+struct Replica {
+  int16_t n[3];      // replica offsets (units of the box)
+  int16_t shift[3];  // periodic shift in force-mesh cells
+  uint8_t perm[3];   // new axis d takes old axis perm[d]
+  uint8_t flip;      // bit d: flip axis d
+};
+
+struct LensShell {
+  double chi_lo2, chi_hi2; // squared shell bounds (Mpc/h)^2
+  double d1_next, gp_half; // D1(a_{i+1}), g_p(a_{i+1/2})
+  int nrep;
+  Replica rep[kMaxReplicas];
+};
+
+// workspace layout (byte offsets)
+struct Layout {
+  size_t cell, frac, mom, fmesh, smesh, maps, flags, sqrtp, tab_d1, tab_inva;
+  size_t scratch;  // start of the scratch union
+  // step scratch
+  size_t rho, cbuf, ubuf;
+  // IC scratch (aliases step scratch)
+  size_t ic_real, ic_cbuf, ic_u, ic_out;
+  // adjoint storage
+  size_t adj;
+  size_t total;
+};
+
+}  // namespace pmlens
+
+struct pm_ctx {
+  pm_config cfg;
+  cudaStream_t stream;
+  int prec;        // PM_FP32 / PM_FP64
+  int rsz;         // sizeof(real)
+  int nc, M;       // particle grid, mesh
+  long long np;    // particles
+  int P, Pc;       // complex row pitch (mesh, particle grid)
+  long long mesh_elems, cmesh_elems, cgrid_elems;
+  int nout_step;   // complex outputs of the step's spectral pass (3 or 6)
+  char* ws;
+  size_t ws_bytes;
+  pmlens::Layout L;
+  pmlens::Cosmo cosmo;
+  std::vector<double> a, ah, kick, drift;
+  std::vector<double> chi_a;   // chi(a_i)
+  std::vector<double> chi_s;   // source distances
+  double chi_tab_max, chi_tab_h;
+  double mean_term[PM_MAX_ZS];
+  int next_step;     // next pm_step index; -1 before pm_ic
+  int last_stepped;  // index of the last pm_step, -1 none
+  int projected;     // last projected shell
+  int pgd_valid;     // PGD meshes valid for last_stepped
+  int ic_done;
+};
+
+namespace pmlens {
+
+// ---------------------------------------------------------------- launchers
+// FFT (fft.cu)
+inline bool fft_supported(int n) {
+  switch (n) {
+    case 32: case 64: case 96: case 128: case 192: case 256: case 512: case 1024: return true;
+    default: return false;
+  }
+}
+// real [n][n][n] -> spectrum [n][n][P] (forward, sign -1, unnormalised)
+template <typename R>
+cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s);
+// spectral operators applied in the fused z pass: out_o = mult_o(k) * spectrum
+enum SpecOp { OP_FORCE = 0, OP_FORCE_PGD = 1, OP_LPT1 = 2, OP_LPT2_DERIV = 3, OP_GRAD_NEG = 4,
+              OP_IDENTITY = 5 };
+struct SpecParams {
+  int op;
+  double kf;        // 2 pi / L
+  double scale;     // global factor (includes 1/n^3)
+  double pgd_scale; // alpha * (M/L) / n^3
+  double kl, ks, nexp;
+  const double* sqrtp;  // table indexed by integer |n|^2 (OP_LPT*)
+};
+// forward x,y passes of `real`, fused z pass (forward, multiply, inverse) into
+// nout complex buffers, then inverse y,x passes into the real outputs.
+template <typename R>
+cudaError_t spectral_apply(const R* real_in, void* cbuf, void* const* ubufs, R* const* real_out,
+                           int nout, int n, int P, const SpecParams& sp, cudaStream_t s);
+
+// particles (particles.cu)
+template <typename R>
+cudaError_t launch_ic_particles(pm_ctx* c, R* const* psi1, R* const* psi2, double d1, double d2,
+                                double gp1, double gp2);
+template <typename R>
+cudaError_t launch_paint(pm_ctx* c, R* rho);
+template <typename R>
+cudaError_t launch_kdk_paint(pm_ctx* c, R* rho, double ckick, double cdrift);
+template <typename R>
+cudaError_t launch_readout(pm_ctx* c, R* const* meshes, double scale, double* out);
+template <typename R>
+cudaError_t launch_set_particles(pm_ctx* c, const double* x, const double* p);
+template <typename R>
+cudaError_t launch_get_particles(pm_ctx* c, double* x, double* p);
+template <typename R>
+cudaError_t launch_lpt2_source(pm_ctx* c, R* const* d, R* src, long long n);
+template <typename R>
+cudaError_t launch_convert_in(const double* in, R* out, long long n, cudaStream_t s);
+template <typename R>
+cudaError_t launch_convert_out(const R* in, double* out, long long n, double scale, cudaStream_t s);
+
+// lensing (lens.cu)
+template <typename R>
+cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd);
+cudaError_t launch_kappa_finalize(pm_ctx* c, double* out);
+
+// helpers
+inline char* ws_ptr(pm_ctx* c, size_t off) { return c->ws + off; }
+inline int* flags_ptr(pm_ctx* c) { return reinterpret_cast<int*>(c->ws + c->L.flags); }
+
+}  // namespace pmlens
