@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 particle-mesh lensing forward model.
+
+One bench step = one whole forward simulation of the workload (initial
+conditions, every kick-drift-kick step with PGD and lightcone projection, and
+the final kappa maps): every row of the hot path.  The metric is particle-steps
+per second = N_particles * N_steps / (seconds per simulation).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+N > 1 runs under torchrun: one independent simulation per GPU (ensemble
+sharding, no data-path collective; "scaling": "weak"), value = the particle
+steps of all ranks / the slowest rank's time.  `--impl reference` times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-steps/s fwd and fwd+adjoint at 256^3 vs plain path; serve p50/p99 latency"
+UNIT = "particle-steps/s"
+WORKLOAD_DESC = {
+    "pm256": "256^3 particles, 512^3 mesh, 256 Mpc/h, 2LPT at a=0.1, 40 KDK steps, PGD on, "
+             "replicated lightcone to z_s in {0.5,1,1.5,2}, 2048^2 maps over 5x5 deg",
+    "pm64": "64^3 particles, 64^3 mesh, 128 Mpc/h, 1LPT at a=0.1, 10 steps, z_s=1, 64^2 map over 2x2 deg",
+    "pm128_vjp": "128^3 particles, 256^3 mesh, 200 Mpc/h, 20 steps, z_s=1, 1024^2 map over 4x4 deg",
+    "pm512": "512^3 particles, 1024^3 mesh, 512 Mpc/h, 40 steps, 8 sources to z=2.5, 4096^2 maps, PGD on",
+}
+
+
+def args_():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="pm256")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nc", type=int, default=None, help="override particles per side (profiling cases)")
+    ap.add_argument("--pgd", type=int, default=None, help="override PGD on/off (profiling cases)")
+    return ap.parse_args()
+
+
+def bench_workload(a):
+    from pm_inputs import workload
+    over = {}
+    if a.nc is not None:
+        over["nc"] = a.nc
+    if a.pgd is not None:
+        over["pgd"] = a.pgd
+    return workload(a.workload, **over)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{self.gpu}.csv")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------- CPU baseline
+def cpu_baseline_sample(w, seed=0):
+    """The FP64 oracle as it stands on one kick-drift step + PM force of the
+    workload's particle count and mesh (the unit of the metric)."""
+    from oracle.cosmology import Cosmology
+    from oracle.lpt import lattice
+    from oracle.nbody import PMState, Stepper, kdk_step
+    rng = np.random.default_rng(seed)
+    nc, M, L = w["nc"], w["nmesh"], w["box"]
+    cosmo = Cosmology(w["omega_m"], w["sigma8"], w["h"], w["n_s"], w["omega_b"], w["t_cmb"])
+    st = Stepper(cosmo, w["a_init"], w["nsteps"])
+    x = np.mod(lattice(nc, L, M) + rng.normal(0, 1.0, size=(nc ** 3, 3)), L)
+    p = rng.normal(0, 1.0, size=(nc ** 3, 3))
+    f = rng.normal(0, 1.0, size=(nc ** 3, 3))
+    t0 = time.perf_counter()
+    kdk_step(PMState(x, p, f), 0, st, nc, M, L)
+    dt = time.perf_counter() - t0
+    return nc ** 3 / dt, dt
+
+
+def run_reference(a, rank, world):
+    if rank != 0:
+        return
+    w = bench_workload(a)
+    for _ in range(a.warmup):
+        cpu_baseline_sample(w)
+    times = []
+    for k in range(a.steps):
+        _, dt = cpu_baseline_sample(w, seed=k)
+        times.append(dt)
+    t = sum(times) / len(times)
+    v = w["nc"] ** 3 / t
+    sample = (f"one kick-drift step with the PM force (paint, FFT Poisson+gradient, 3 inverse FFTs, "
+              f"readout) of {w['nc']}^3 particles on the {w['nmesh']}^3 mesh per step, FP64 numpy")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{a.workload}: {WORKLOAD_DESC.get(a.workload, '')}",
+                       "sample": "per step: " + sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+def run_gpu(a, rank, world, local_rank):
+    import torch
+
+    from paper_2012_07266_gb300.api import PM_FP32, PM_FP64, Simulation
+    from pm_inputs import white_noise
+
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    w = bench_workload(a)
+    prec = PM_FP64 if a.precision == "fp64" else PM_FP32
+    stream = torch.cuda.Stream(dev)
+    sim = Simulation(device=dev, stream=stream, precision=prec, **w)
+    noise = torch.from_numpy(white_noise(w["nc"], w["noise_seed"] + rank)).to(dev)
+    npart, nsteps = w["nc"] ** 3, w["nsteps"]
+
+    def one():
+        sim.run(noise)  # kappa_maps synchronises the stream
+
+    for _ in range(a.warmup):
+        one()
+    sim.profile_read()
+    sim.profile(True)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(a.steps):
+        one()
+    ev1.record(stream)
+    ev1.synchronize()
+    barrier()
+    clk = clocks.stop()
+    sim.profile(False)
+    prof = sim.profile_read()
+    ms = ev0.elapsed_time(ev1) / a.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * npart * nsteps / (ms * 1e-3)
+    launches = sum(v[1] for v in prof.values())
+
+    # end to end through the public API with host buffers (pinned)
+    e2e = None
+    if not a.no_e2e:
+        h_noise = torch.from_numpy(white_noise(w["nc"], w["noise_seed"] + rank)).pin_memory()
+        h_kappa = torch.empty((sim.n_zs, sim.npix, sim.npix), dtype=torch.float64).pin_memory()
+        d_noise = torch.empty_like(h_noise, device=dev)
+        d_kappa = torch.empty((sim.n_zs, sim.npix, sim.npix), dtype=torch.float64, device=dev)
+
+        def one_e2e():
+            with torch.cuda.stream(stream):
+                d_noise.copy_(h_noise, non_blocking=True)
+                sim.ic(d_noise)
+                for i in range(nsteps):
+                    sim.step(i)
+                    sim.lens_project(i)
+                sim.kappa_maps(d_kappa)
+                h_kappa.copy_(d_kappa, non_blocking=True)
+            stream.synchronize()
+
+        one_e2e()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(a.steps):
+            one_e2e()
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        ems = e0.elapsed_time(e1) / a.steps
+        if dist is not None:
+            t = torch.tensor([ems], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ems = float(t.item())
+        e2e = {"value": world * npart * nsteps / (ems * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": h_noise.numel() * 8, "d2h_bytes_per_step": h_kappa.numel() * 8}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_src = peaks()
+    kern = {}
+    for k, (kms, n, b) in prof.items():
+        if n == 0:
+            continue
+        kern[k] = {"launches": n, "ms_total": round(kms, 3),
+                   "ms_per_launch": round(kms / n, 4) if kms else None,
+                   "gbs": round(b / (kms * 1e-3) / 1e9, 1) if kms > 0 and b > 0 else None,
+                   "share": None}
+    tot = sum(v["ms_total"] for v in kern.values())
+    for v in kern.values():
+        v["share"] = round(v["ms_total"] / tot, 4) if tot else None
+    dom = max((k for k in kern if prof[k][2] > 0), key=lambda k: kern[k]["ms_total"])
+    dms, dn, db = prof[dom]
+    achieved = db / dn / (dms / dn * 1e-3) / 1e9
+    traffic = read_traffic(dom, a.workload)
+    roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_source": peak_src,
+            "algo_bytes_per_launch": db / dn, "traffic": traffic}
+    cpu = None
+    if not a.no_cpu_baseline and world == 1:
+        v, dt = cpu_baseline_sample(w)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one FP64 oracle kick-drift step with PM force of {w['nc']}^3 particles on the "
+                         f"{w['nmesh']}^3 mesh ({dt:.1f} s), single-threaded numpy"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == PM_FP32 else "f64", "data": "synthetic",
+            "config": {"workload": f"{a.workload}: {WORKLOAD_DESC.get(a.workload, '')}",
+                       "step": "one whole forward simulation (IC, all KDK steps, PGD, lightcone, kappa)",
+                       "l2": "inputs larger than L2 (workspace %.1f GB)" % (sim.nbytes / 1e9),
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
+            "cpu_baseline": cpu, "kernels": kern}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def read_traffic(kernel, workload):
+    """Per-launch DRAM bytes of `kernel` from a committed ncu summary, if its
+    source hash still matches the current kernels (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) == 4 and parts[0] == kernel and parts[1] == workload and parts[3] == want:
+            return float(parts[2])
+    return None
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2012_07266_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    a = args_()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_gpu(a, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

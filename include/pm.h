@@ -168,6 +168,25 @@ pm_status pm_get_density(pm_ctx* ctx, double* d_rho);
 /* Synchronise the stream and report the sticky device error flag. */
 pm_status pm_sync_status(pm_ctx* ctx);
 
+/* ---- instrumentation (no counterpart in the paper) --------------------- */
+
+/* Turn per-kernel CUDA-event timing on (1) or off (0).  Kernel launches are
+ * always counted per kernel class; with timing on, each launch is bracketed
+ * by two events recorded on the context's stream.  Synchronises the stream. */
+pm_status pm_profile(pm_ctx* ctx, int32_t enable);
+
+/* Per-class totals since the last read, each a host array of nkinds
+ * entries (any pointer may be NULL): kernel time in ms (0 unless timing was
+ * on), launch counts, and algorithmic HBM bytes of those launches (the bytes
+ * the operation must move: each pass's input read and output written once,
+ * gathered meshes once, particle state once).  Synchronises the stream, then
+ * resets the counters. */
+pm_status pm_profile_read(pm_ctx* ctx, double* ms, int64_t* launches, double* bytes, int32_t nkinds);
+
+/* Number of kernel classes and the static name of class `kind`. */
+int32_t pm_kernel_kinds(void);
+const char* pm_kernel_name(int32_t kind);
+
 #ifdef __cplusplus
 }
 #endif

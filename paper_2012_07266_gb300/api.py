@@ -123,3 +123,16 @@ class Simulation:
 
     def sync(self):
         lib.call("pm_sync_status", self.ctx)
+
+    def profile(self, enable: bool):
+        lib.call("pm_profile", self.ctx, int(bool(enable)))
+
+    def profile_read(self):
+        """{kernel class: (ms, launches, algorithmic bytes)} since the last read (synchronises)."""
+        names = lib.kernel_names()
+        ms = (C.c_double * len(names))()
+        n = (C.c_int64 * len(names))()
+        b = (C.c_double * len(names))()
+        lib.call("pm_profile_read", self.ctx, C.cast(ms, C.c_void_p), C.cast(n, C.c_void_p),
+                 C.cast(b, C.c_void_p), len(names))
+        return {k: (ms[i], int(n[i]), b[i]) for i, k in enumerate(names)}

@@ -28,6 +28,7 @@ UNITS = [
     ("lens.cu", "lens.o", []),
     ("capi.cu", "capi.o", []),
     ("cosmo.cpp", "cosmo.o", []),
+    ("prof.cpp", "prof.o", []),
 ]
 
 

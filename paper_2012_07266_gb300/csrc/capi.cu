@@ -165,7 +165,8 @@ cudaError_t force_from_rho(pm_ctx* c, bool with_pgd, double alpha_pgd) {
     R* S = rp<R>(c, c->L.smesh);
     for (int o = 0; o < 3; ++o) outs[3 + o] = S + o * c->mesh_elems;
   }
-  return spectral_apply<R>(rp<R>(c, c->L.rho), c->ws + c->L.cbuf, ub, outs, nout, c->M, c->P, sp, c->stream);
+  return spectral_apply<R>(rp<R>(c, c->L.rho), c->ws + c->L.cbuf, ub, outs, nout, c->M, c->P, sp, c->stream,
+                           &c->prof);
 }
 
 bool shell_active(pm_ctx* c, int i) {
@@ -182,7 +183,7 @@ pm_status do_ic(pm_ctx* c, const double* d_noise) {
   cudaStream_t s = c->stream;
   const long long g = (long long)c->nc * c->nc * c->nc;
   R* noise = rp<R>(c, c->L.ic_real);
-  cudaError_t e = launch_convert_in<R>(d_noise, noise, g, s);
+  cudaError_t e = launch_convert_in<R>(d_noise, noise, g, s, &c->prof);
   if (e) return PM_ERR_CUDA;
   const int nout = cfg.lpt_order == 2 ? 9 : 3;
   void* ub[9];
@@ -195,13 +196,15 @@ pm_status do_ic(pm_ctx* c, const double* d_noise) {
   sp.kf = 2.0 * M_PI / cfg.box;
   sp.scale = 1.0 / (double)g;
   sp.sqrtp = reinterpret_cast<const double*>(c->ws + c->L.sqrtp);
-  if ((e = spectral_apply<R>(noise, c->ws + c->L.ic_cbuf, ub, outs, nout, c->nc, c->Pc, sp, s))) return PM_ERR_CUDA;
+  if ((e = spectral_apply<R>(noise, c->ws + c->L.ic_cbuf, ub, outs, nout, c->nc, c->Pc, sp, s, &c->prof, KK_IC)))
+    return PM_ERR_CUDA;
   R* const* psi2 = nullptr;
   if (cfg.lpt_order == 2) {
     if ((e = launch_lpt2_source<R>(c, outs + 3, outs[9], g))) return PM_ERR_CUDA;
     SpecParams sp2 = sp;
     sp2.op = OP_GRAD_NEG;
-    if ((e = spectral_apply<R>(outs[9], c->ws + c->L.ic_cbuf, ub, outs + 10, 3, c->nc, c->Pc, sp2, s)))
+    if ((e = spectral_apply<R>(outs[9], c->ws + c->L.ic_cbuf, ub, outs + 10, 3, c->nc, c->Pc, sp2, s, &c->prof,
+                               KK_IC)))
       return PM_ERR_CUDA;
     psi2 = outs + 10;
   }
@@ -343,9 +346,10 @@ pm_status do_readout(pm_ctx* c, size_t off, double* out) {
 template <typename R>
 pm_status do_fft(pm_ctx* c, const double* in, double* out) {
   R* rho = rp<R>(c, c->L.rho);
-  if (launch_convert_in<R>(in, rho, c->mesh_elems, c->stream)) return PM_ERR_CUDA;
-  if (fft3d_r2c<R>(rho, c->ws + c->L.cbuf, c->M, c->P, c->stream)) return PM_ERR_CUDA;
+  if (launch_convert_in<R>(in, rho, c->mesh_elems, c->stream, &c->prof)) return PM_ERR_CUDA;
+  if (fft3d_r2c<R>(rho, c->ws + c->L.cbuf, c->M, c->P, c->stream, &c->prof)) return PM_ERR_CUDA;
   using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+  ProfScope ps(&c->prof, KK_MISC, c->stream);
   k_unpad_complex<R><<<1024, 256, 0, c->stream>>>(reinterpret_cast<const C*>(c->ws + c->L.cbuf), out, c->M, c->P);
   return cuda_status(cudaGetLastError());
 }
@@ -355,7 +359,7 @@ pm_status do_density(pm_ctx* c, double* out) {
   R* rho = rp<R>(c, c->L.rho);
   if (cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, c->stream)) return PM_ERR_CUDA;
   if (launch_paint<R>(c, rho)) return PM_ERR_CUDA;
-  return cuda_status(launch_convert_out<R>(rho, out, c->mesh_elems, 1.0, c->stream));
+  return cuda_status(launch_convert_out<R>(rho, out, c->mesh_elems, 1.0, c->stream, &c->prof));
 }
 
 }  // namespace
@@ -529,5 +533,35 @@ pm_status pm_sync_status(pm_ctx* c) {
   if (!c) return PM_ERR_ARG;
   return read_flags(c);
 }
+
+pm_status pm_profile(pm_ctx* c, int32_t enable) {
+  if (!c) return PM_ERR_ARG;
+  if (cudaStreamSynchronize(c->stream)) return PM_ERR_CUDA;
+  c->prof.resolve();
+  c->prof.timing = enable != 0;
+  return PM_OK;
+}
+
+pm_status pm_profile_read(pm_ctx* c, double* ms, int64_t* launches, double* bytes, int32_t nkinds) {
+  if (!c || nkinds < 0) return PM_ERR_ARG;
+  if (cudaStreamSynchronize(c->stream)) return PM_ERR_CUDA;
+  c->prof.resolve();
+  for (int k = 0; k < nkinds && k < KK_COUNT; ++k) {
+    if (ms) ms[k] = c->prof.ms[k];
+    if (launches) launches[k] = c->prof.launches[k];
+    if (bytes) bytes[k] = c->prof.bytes[k];
+  }
+  for (int k = 0; k < KK_COUNT; ++k) {
+    c->prof.ms[k] = 0.0;
+    c->prof.launches[k] = 0;
+    c->prof.bytes[k] = 0.0;
+    c->prof.timed[k] = 0;
+  }
+  return PM_OK;
+}
+
+int32_t pm_kernel_kinds(void) { return KK_COUNT; }
+
+const char* pm_kernel_name(int32_t kind) { return kernel_kind_name(kind); }
 
 }  // extern "C"

@@ -8,6 +8,9 @@ namespace {
 template <typename R, int N>
 struct Launch {
   using C = typename CT<R>::T;
+  // algorithmic bytes of one pass: real mesh R, unpadded half-spectrum C
+  static constexpr double RB = (double)N * N * N * sizeof(R);
+  static constexpr double CB = (double)N * N * (N / 2 + 1) * sizeof(C);
   static size_t smem_x() { return (size_t)(N / 2 + RowTile<R, N>::ROWS * (N / 2 + 1)) * sizeof(C); }
   static size_t smem_cols() { return (size_t)(N + N * ColTile<R, N>::W) * sizeof(C); }
   static size_t smem_z() { return (size_t)(N + 2 * N * ColTile<R, N>::W) * sizeof(C); }
@@ -24,51 +27,57 @@ struct Launch {
     done = true;
   }
 
-  static void x_fwd(const R* in, C* out, int P, cudaStream_t s) {
+  static void x_fwd(const R* in, C* out, int P, cudaStream_t s, Prof* pf, int kind) {
+    ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_X_FWD, s, RB + CB);
     k_fft_x_r2c<R, N><<<(long long)N * N / RowTile<R, N>::ROWS, RowTile<R, N>::THREADS, smem_x(), s>>>(in, out, P);
   }
-  static void x_inv(const C* in, R* out, int P, cudaStream_t s) {
+  static void x_inv(const C* in, R* out, int P, cudaStream_t s, Prof* pf, int kind) {
+    ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_X_INV, s, RB + CB);
     k_fft_x_c2r<R, N><<<(long long)N * N / RowTile<R, N>::ROWS, RowTile<R, N>::THREADS, smem_x(), s>>>(in, out, P);
   }
   // y pass: planes = z (stride N*P), rows = y (stride P)
-  static void y(C* d, int P, bool inv, cudaStream_t s) {
+  static void y(C* d, int P, bool inv, cudaStream_t s, Prof* pf, int kind) {
+    ProfScope ps(pf, kind >= 0 ? kind : (inv ? KK_FFT_Y_INV : KK_FFT_Y_FWD), s, 2 * CB);
     dim3 g(ntiles(), N);
     if (inv) k_fft_cols<R, N, true><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, (long long)N * P, P, N / 2 + 1);
     else k_fft_cols<R, N, false><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, (long long)N * P, P, N / 2 + 1);
   }
   // z pass: planes = y (stride P), rows = z (stride N*P)
-  static void z(C* d, int P, bool inv, cudaStream_t s) {
+  static void z(C* d, int P, bool inv, cudaStream_t s, Prof* pf, int kind) {
+    ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_Z_FWD, s, 2 * CB);
     dim3 g(ntiles(), N);
     if (inv) k_fft_cols<R, N, true><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, P, (long long)N * P, N / 2 + 1);
     else k_fft_cols<R, N, false><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, P, (long long)N * P, N / 2 + 1);
   }
-  static void zop(const C* in, const OutPtrs& o, int nout, int P, const SpecParams& sp, cudaStream_t s) {
+  static void zop(const C* in, const OutPtrs& o, int nout, int P, const SpecParams& sp, cudaStream_t s,
+                  Prof* pf, int kind) {
+    ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_Z_OP, s, (1 + nout) * CB);
     dim3 g(ntiles(), N);
     k_zpass_op<R, N><<<g, ColTile<R, N>::THREADS, smem_z(), s>>>(in, o, nout, P, sp);
   }
 
-  static cudaError_t r2c(const R* real, void* cplx, int P, cudaStream_t s) {
+  static cudaError_t r2c(const R* real, void* cplx, int P, cudaStream_t s, Prof* pf) {
     attrs();
     C* c = reinterpret_cast<C*>(cplx);
-    x_fwd(real, c, P, s);
-    y(c, P, false, s);
-    z(c, P, false, s);
+    x_fwd(real, c, P, s, pf, -1);
+    y(c, P, false, s, pf, -1);
+    z(c, P, false, s, pf, -1);
     return cudaGetLastError();
   }
 
   static cudaError_t apply(const R* real_in, void* cbuf, void* const* ubufs, R* const* real_out, int nout, int P,
-                           const SpecParams& sp, cudaStream_t s) {
+                           const SpecParams& sp, cudaStream_t s, Prof* pf, int kind) {
     attrs();
     C* c = reinterpret_cast<C*>(cbuf);
-    x_fwd(real_in, c, P, s);
-    y(c, P, false, s);
+    x_fwd(real_in, c, P, s, pf, kind);
+    y(c, P, false, s, pf, kind);
     OutPtrs o;
     for (int i = 0; i < 9; ++i) o.p[i] = i < nout ? ubufs[i] : nullptr;
-    zop(c, o, nout, P, sp, s);
+    zop(c, o, nout, P, sp, s, pf, kind);
     for (int i = 0; i < nout; ++i) {
       C* u = reinterpret_cast<C*>(ubufs[i]);
-      y(u, P, true, s);
-      x_inv(u, real_out[i], P, s);
+      y(u, P, true, s, pf, kind);
+      x_inv(u, real_out[i], P, s, pf, kind);
     }
     return cudaGetLastError();
   }
@@ -90,19 +99,19 @@ struct Launch {
 }  // namespace
 
 template <typename R>
-cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s) {
-  PM_FFT_DISPATCH(n, L::r2c(real, cplx, P, s));
+cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s, Prof* pf) {
+  PM_FFT_DISPATCH(n, L::r2c(real, cplx, P, s, pf));
 }
 
 template <typename R>
 cudaError_t spectral_apply(const R* real_in, void* cbuf, void* const* ubufs, R* const* real_out, int nout, int n,
-                           int P, const SpecParams& sp, cudaStream_t s) {
+                           int P, const SpecParams& sp, cudaStream_t s, Prof* pf, int kind) {
   if (nout < 1 || nout > 9) return cudaErrorInvalidValue;
-  PM_FFT_DISPATCH(n, L::apply(real_in, cbuf, ubufs, real_out, nout, P, sp, s));
+  PM_FFT_DISPATCH(n, L::apply(real_in, cbuf, ubufs, real_out, nout, P, sp, s, pf, kind));
 }
 
-template cudaError_t fft3d_r2c<PM_REAL>(const PM_REAL*, void*, int, int, cudaStream_t);
+template cudaError_t fft3d_r2c<PM_REAL>(const PM_REAL*, void*, int, int, cudaStream_t, Prof*);
 template cudaError_t spectral_apply<PM_REAL>(const PM_REAL*, void*, void* const*, PM_REAL* const*, int, int, int,
-                                              const SpecParams&, cudaStream_t);
+                                              const SpecParams&, cudaStream_t, Prof*, int);
 
 }  // namespace pmlens

@@ -196,6 +196,9 @@ cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
   for (int q = 0; q < sh.nrep; ++q) A.rep[q] = sh.rep[q];
   long long blocks = (c->np + 255) / 256;
   if (blocks > 152LL * 8) blocks = 152LL * 8;
+  // particle state read once (+ three PGD meshes gathered)
+  ProfScope ps(&c->prof, KK_LENS, c->stream,
+               c->np * (4.0 + 6.0 * sizeof(R)) + (use_pgd ? 3.0 * c->mesh_elems * sizeof(R) : 0.0));
   k_lens<R><<<(int)blocks, 256, 0, c->stream>>>(A);
   return cudaGetLastError();
 }
@@ -206,6 +209,7 @@ cudaError_t launch_kappa_finalize(pm_ctx* c, double* out) {
   for (int s = 0; s < PM_MAX_ZS; ++s) mt.v[s] = s < c->cfg.n_zs ? c->mean_term[s] : 0.0;
   long long blocks = (npix2 * c->cfg.n_zs + 255) / 256;
   if (blocks > 152LL * 8) blocks = 152LL * 8;
+  ProfScope ps(&c->prof, KK_MISC, c->stream);
   k_kappa_finalize<<<(int)blocks, 256, 0, c->stream>>>(reinterpret_cast<const double*>(c->ws + c->L.maps), out,
                                                        npix2, c->cfg.n_zs, mt, flags_ptr(c));
   return cudaGetLastError();

@@ -247,6 +247,7 @@ template <typename R>
 cudaError_t launch_ic_particles(pm_ctx* c, R* const* psi1, R* const* psi2, double d1, double d2, double gp1,
                                 double gp2) {
   const double cpl = c->M / c->cfg.box;
+  ProfScope ps(&c->prof, KK_IC, c->stream);
   k_ic_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(
       pstate<R>(c), psi1[0], psi1[1], psi1[2], psi2 ? psi2[0] : nullptr, psi2 ? psi2[1] : nullptr,
       psi2 ? psi2[2] : nullptr, c->nc, c->M, cpl, d1, d2, gp1, gp2, c->np);
@@ -256,6 +257,7 @@ cudaError_t launch_ic_particles(pm_ctx* c, R* const* psi1, R* const* psi2, doubl
 template <typename R>
 cudaError_t launch_paint(pm_ctx* c, R* rho) {
   const double mass = std::pow((double)c->M / c->nc, 3.0);
+  ProfScope ps(&c->prof, KK_PAINT, c->stream, c->np * (4.0 + 3.0 * sizeof(R)) + c->mesh_elems * (double)sizeof(R));
   k_paint<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), rho, c->M, (R)mass, c->np);
   return cudaGetLastError();
 }
@@ -264,6 +266,9 @@ template <typename R>
 cudaError_t launch_kdk_paint(pm_ctx* c, R* rho, double ckick, double cdrift) {
   const double mass = std::pow((double)c->M / c->nc, 3.0);
   R* F = reinterpret_cast<R*>(c->ws + c->L.fmesh);
+  // state read + written, three force meshes gathered, density written
+  ProfScope ps(&c->prof, KK_KDK_PAINT, c->stream,
+               2.0 * c->np * (4.0 + 6.0 * sizeof(R)) + 4.0 * c->mesh_elems * (double)sizeof(R));
   k_kdk_paint<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), F, F + c->mesh_elems,
                                                                F + 2 * c->mesh_elems, rho, c->M, (R)ckick,
                                                                (R)cdrift, (R)mass, c->np);
@@ -272,6 +277,7 @@ cudaError_t launch_kdk_paint(pm_ctx* c, R* rho, double ckick, double cdrift) {
 
 template <typename R>
 cudaError_t launch_readout(pm_ctx* c, R* const* meshes, double scale, double* out) {
+  ProfScope ps(&c->prof, KK_MISC, c->stream);
   k_readout<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), meshes[0], meshes[1], meshes[2], c->M,
                                                              scale, out, c->np);
   return cudaGetLastError();
@@ -279,6 +285,7 @@ cudaError_t launch_readout(pm_ctx* c, R* const* meshes, double scale, double* ou
 
 template <typename R>
 cudaError_t launch_set_particles(pm_ctx* c, const double* x, const double* p) {
+  ProfScope ps(&c->prof, KK_MISC, c->stream);
   k_set_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), x, p, c->M, c->M / c->cfg.box,
                                                                    c->np);
   return cudaGetLastError();
@@ -286,24 +293,28 @@ cudaError_t launch_set_particles(pm_ctx* c, const double* x, const double* p) {
 
 template <typename R>
 cudaError_t launch_get_particles(pm_ctx* c, double* x, double* p) {
+  ProfScope ps(&c->prof, KK_MISC, c->stream);
   k_get_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), x, p, c->cfg.box / c->M, c->np);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_lpt2_source(pm_ctx* c, R* const* d, R* src, long long n) {
+  ProfScope ps(&c->prof, KK_IC, c->stream);
   k_lpt2_source<R><<<grid_for(n, 256), 256, 0, c->stream>>>(d[0], d[1], d[2], d[3], d[4], d[5], src, n);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_convert_in(const double* in, R* out, long long n, cudaStream_t s) {
+cudaError_t launch_convert_in(const double* in, R* out, long long n, cudaStream_t s, Prof* pf) {
+  ProfScope ps(pf, KK_MISC, s);
   k_convert_in<R><<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_convert_out(const R* in, double* out, long long n, double scale, cudaStream_t s) {
+cudaError_t launch_convert_out(const R* in, double* out, long long n, double scale, cudaStream_t s, Prof* pf) {
+  ProfScope ps(pf, KK_MISC, s);
   k_convert_out<R><<<grid_for(n, 256), 256, 0, s>>>(in, out, n, scale);
   return cudaGetLastError();
 }
@@ -316,8 +327,8 @@ cudaError_t launch_convert_out(const R* in, double* out, long long n, double sca
   template cudaError_t launch_set_particles<R>(pm_ctx*, const double*, const double*);                    \
   template cudaError_t launch_get_particles<R>(pm_ctx*, double*, double*);                                \
   template cudaError_t launch_lpt2_source<R>(pm_ctx*, R* const*, R*, long long);                          \
-  template cudaError_t launch_convert_in<R>(const double*, R*, long long, cudaStream_t);                   \
-  template cudaError_t launch_convert_out<R>(const R*, double*, long long, double, cudaStream_t);
+  template cudaError_t launch_convert_in<R>(const double*, R*, long long, cudaStream_t, Prof*);            \
+  template cudaError_t launch_convert_out<R>(const R*, double*, long long, double, cudaStream_t, Prof*);
 PM_INST(float)
 PM_INST(double)
 

@@ -55,6 +55,40 @@ struct LensShell {
   Replica rep[kMaxReplicas];
 };
 
+// kernel classes for launch counting and optional event timing
+enum KernelKind {
+  KK_KDK_PAINT = 0, KK_PAINT, KK_FFT_X_FWD, KK_FFT_Y_FWD, KK_FFT_Z_FWD, KK_FFT_Z_OP, KK_FFT_Y_INV,
+  KK_FFT_X_INV, KK_LENS, KK_IC, KK_MISC, KK_ADJ, KK_COUNT
+};
+const char* kernel_kind_name(int k);
+
+// Per-context launch counter and CUDA-event timer.  When timing is on, each
+// launch is bracketed by two events recorded on the launching stream; the
+// elapsed times are resolved on read.
+struct Prof {
+  bool timing = false;
+  long long launches[KK_COUNT] = {};
+  double ms[KK_COUNT] = {};
+  double bytes[KK_COUNT] = {};  // algorithmic HBM bytes of the counted launches
+  long long timed[KK_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  struct Rec { int kind; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  cudaEvent_t get();
+  void resolve();
+  ~Prof();
+};
+
+struct ProfScope {
+  Prof* p;
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  ProfScope(Prof* p_, int k, cudaStream_t s_, double algo_bytes = 0.0);
+  ~ProfScope();
+};
+
 // workspace layout (byte offsets)
 struct Layout {
   size_t cell, frac, mom, fmesh, smesh, maps, flags, sqrtp, tab_d1, tab_inva;
@@ -94,6 +128,7 @@ struct pm_ctx {
   int projected;     // last projected shell
   int pgd_valid;     // PGD meshes valid for last_stepped
   int ic_done;
+  pmlens::Prof prof;
 };
 
 namespace pmlens {
@@ -108,7 +143,7 @@ inline bool fft_supported(int n) {
 }
 // real [n][n][n] -> spectrum [n][n][P] (forward, sign -1, unnormalised)
 template <typename R>
-cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s);
+cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s, Prof* prof);
 // spectral operators applied in the fused z pass: out_o = mult_o(k) * spectrum
 enum SpecOp { OP_FORCE = 0, OP_FORCE_PGD = 1, OP_LPT1 = 2, OP_LPT2_DERIV = 3, OP_GRAD_NEG = 4,
               OP_IDENTITY = 5 };
@@ -122,9 +157,11 @@ struct SpecParams {
 };
 // forward x,y passes of `real`, fused z pass (forward, multiply, inverse) into
 // nout complex buffers, then inverse y,x passes into the real outputs.
+// kind >= 0 books every launch under that class (e.g. KK_IC), else per pass.
 template <typename R>
 cudaError_t spectral_apply(const R* real_in, void* cbuf, void* const* ubufs, R* const* real_out,
-                           int nout, int n, int P, const SpecParams& sp, cudaStream_t s);
+                           int nout, int n, int P, const SpecParams& sp, cudaStream_t s, Prof* prof,
+                           int kind = -1);
 
 // particles (particles.cu)
 template <typename R>
@@ -143,9 +180,9 @@ cudaError_t launch_get_particles(pm_ctx* c, double* x, double* p);
 template <typename R>
 cudaError_t launch_lpt2_source(pm_ctx* c, R* const* d, R* src, long long n);
 template <typename R>
-cudaError_t launch_convert_in(const double* in, R* out, long long n, cudaStream_t s);
+cudaError_t launch_convert_in(const double* in, R* out, long long n, cudaStream_t s, Prof* pf);
 template <typename R>
-cudaError_t launch_convert_out(const R* in, double* out, long long n, double scale, cudaStream_t s);
+cudaError_t launch_convert_out(const R* in, double* out, long long n, double scale, cudaStream_t s, Prof* pf);
 
 // lensing (lens.cu)
 template <typename R>

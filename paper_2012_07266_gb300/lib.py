@@ -20,7 +20,8 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_WORKSPACE", 3: "PM_ERR_CUDA",
 # every symbol include/pm.h declares
 EXPORTS = ["pm_workspace_size", "pm_init", "pm_ic", "pm_step", "lens_project", "kappa_maps",
            "pm_vjp", "pm_destroy", "pm_strerror", "pm_get_particles", "pm_set_particles",
-           "pm_get_forces", "pm_get_pgd", "pm_fft_r2c", "pm_get_density", "pm_sync_status"]
+           "pm_get_forces", "pm_get_pgd", "pm_fft_r2c", "pm_get_density", "pm_sync_status",
+           "pm_profile", "pm_profile_read", "pm_kernel_kinds", "pm_kernel_name"]
 
 
 class PMConfig(C.Structure):
@@ -99,6 +100,8 @@ def load():
         "pm_fft_r2c": [vp, vp, vp],
         "pm_get_density": [vp, vp],
         "pm_sync_status": [vp],
+        "pm_profile": [vp, i32],
+        "pm_profile_read": [vp, vp, vp, vp, i32],
     }
     for name, args in proto.items():
         f = getattr(lib, name)
@@ -106,6 +109,10 @@ def load():
         f.restype = st
     lib.pm_strerror.argtypes = [st]
     lib.pm_strerror.restype = C.c_char_p
+    lib.pm_kernel_kinds.argtypes = []
+    lib.pm_kernel_kinds.restype = i32
+    lib.pm_kernel_name.argtypes = [i32]
+    lib.pm_kernel_name.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -124,3 +131,8 @@ def workspace_size(cfg: PMConfig) -> int:
     n = C.c_size_t(0)
     call("pm_workspace_size", C.byref(cfg), C.byref(n))
     return int(n.value)
+
+
+def kernel_names():
+    so = load()
+    return [so.pm_kernel_name(k).decode() for k in range(so.pm_kernel_kinds())]

@@ -23,7 +23,7 @@ def L():
 def header_functions():
     src = open(os.path.join(ROOT, "include", "pm.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:pm_status|const char\*)\s+(\w+)\s*\(", src, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:pm_status|const char\*|int32_t)\s+(\w+)\s*\(", src, flags=re.M)))
 
 
 def test_exports_every_declared_symbol(L):
