@@ -187,6 +187,32 @@ pm_status pm_profile_read(pm_ctx* ctx, double* ms, int64_t* launches, double* by
 int32_t pm_kernel_kinds(void);
 const char* pm_kernel_name(int32_t kind);
 
+/* ---- allocation-free variant (no counterpart in the paper) -------------- */
+
+/* PM forces F = -(3/2) Omega_m grad(phi) at n particles, like pm_set_particles
+ * followed by pm_get_forces, but without a context or a workspace: for callers
+ * that cannot allocate device memory (code inside a framework whose allocator
+ * owns the device memory, plugins or callbacks that must not allocate,
+ * processes under a hard device-memory budget).  Its scratch meshes live in a
+ * file-scope device array of about 10 MB that every GPU loading the library
+ * holds until the process exits.
+ *  d_x: (n, 3) float64 positions in [0, box) Mpc/h, device, caller-owned.
+ *  d_f: (n, 3) float64 forces out (Mpc/h per unit kick factor), device.
+ *  nmesh: force mesh per side, one of 32 or 64 (larger meshes return
+ *         PM_ERR_UNSUPPORTED before any device work); each particle carries
+ *         mass nmesh^3 / n so that the mean density is 1.  FP32 arithmetic.
+ *  stream: cudaStream_t on which the work is enqueued; the call does not
+ *          synchronise.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  No cudaMalloc/cudaFree or allocating library routine is called.
+ * Every call shares the one array (its previous contents are overwritten;
+ * the density is cleared on each call), so calls that overlap on the GPU --
+ * on different streams or from different threads -- race and must be
+ * serialised by the caller. */
+pm_status pm_forces_static(const double* d_x, int64_t n, int32_t nmesh, double box, double omega_m,
+                           double* d_f, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

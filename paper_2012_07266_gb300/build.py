@@ -29,6 +29,7 @@ UNITS = [
     ("capi.cu", "capi.o", []),
     ("cosmo.cpp", "cosmo.o", []),
     ("prof.cpp", "prof.o", []),
+    ("static_forces.cu", "static_forces.o", []),
 ]
 
 

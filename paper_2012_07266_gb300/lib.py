@@ -21,7 +21,8 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_WORKSPACE", 3: "PM_ERR_CUDA",
 EXPORTS = ["pm_workspace_size", "pm_init", "pm_ic", "pm_step", "lens_project", "kappa_maps",
            "pm_vjp", "pm_destroy", "pm_strerror", "pm_get_particles", "pm_set_particles",
            "pm_get_forces", "pm_get_pgd", "pm_fft_r2c", "pm_get_density", "pm_sync_status",
-           "pm_profile", "pm_profile_read", "pm_kernel_kinds", "pm_kernel_name"]
+           "pm_profile", "pm_profile_read", "pm_kernel_kinds", "pm_kernel_name",
+           "pm_forces_static"]
 
 
 class PMConfig(C.Structure):
@@ -102,6 +103,7 @@ def load():
         "pm_sync_status": [vp],
         "pm_profile": [vp, i32],
         "pm_profile_read": [vp, vp, vp, vp, i32],
+        "pm_forces_static": [vp, C.c_int64, i32, C.c_double, C.c_double, vp, vp],
     }
     for name, args in proto.items():
         f = getattr(lib, name)
