@@ -30,6 +30,7 @@ UNITS = [
     ("cosmo.cpp", "cosmo.o", []),
     ("prof.cpp", "prof.o", []),
     ("static_forces.cu", "static_forces.o", []),
+    ("adjoint.cu", "adjoint.o", []),
 ]
 
 

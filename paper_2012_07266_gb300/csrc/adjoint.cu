@@ -1,0 +1,439 @@
+// Adjoint (reverse-mode) kernels of the PM lensing model.
+//
+// Transposes of the forward kernels, written by hand (Sec. 3: the model is
+// differentiated with respect to the initial modes; Appendix A: Omega_m and
+// sigma_8):
+//  * CIC paint <-> readout: the cotangent of a readout is painted with the
+//    cotangent as weight; the position derivative of a readout is the CIC
+//    weight derivative (-1 / +1 along the axis) times the mesh values;
+//  * the spectral operators (Poisson + gradient, PGD filter, LPT operators)
+//    are transposed in the fused z pass with the conjugate multiplier
+//    (fft_impl.cuh, k_zpass_combine);
+//  * the lightcone projection's transpose follows the forward kernel step by
+//    step and returns d/dx, d/dp and d/dS per particle;
+//  * reductions (dot products) for sigma_8 and for the Omega_m finite
+//    differences accumulate in FP64.
+// All particle quantities are in force-mesh cell units, as in the forward.
+#include <algorithm>
+#include <cmath>
+
+#include "adjoint.h"
+
+namespace pmlens {
+
+namespace {
+
+__device__ __forceinline__ void unpack3(uint32_t c, int* i) {
+  i[0] = c & 1023u;
+  i[1] = (c >> 10) & 1023u;
+  i[2] = c >> 20;
+}
+
+__device__ __forceinline__ double interp_t(const double* __restrict__ t, int n, double hinv, double x) {
+  double u = x * hinv;
+  int k = (int)u;
+  if (k < 0) k = 0;
+  if (k > n - 2) k = n - 2;
+  const double f = u - k;
+  return t[k] * (1.0 - f) + t[k + 1] * f;
+}
+
+// block-wide sum of one double into *acc (one atomic per block)
+__device__ __forceinline__ void block_add(double v, double* acc) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(acc, v);
+  }
+  __syncthreads();
+}
+
+struct CIC {
+  long long o[8];
+  int valid;
+};
+
+template <typename R>
+__device__ __forceinline__ void cic_offsets(const int* i, int M, long long* o) {
+  const int x1 = i[0] + 1 == M ? 0 : i[0] + 1, y1 = i[1] + 1 == M ? 0 : i[1] + 1, z1 = i[2] + 1 == M ? 0 : i[2] + 1;
+  const int xs[2] = {i[0], x1}, ys[2] = {i[1], y1}, zs[2] = {i[2], z1};
+#pragma unroll
+  for (int c = 0; c < 8; ++c) o[c] = ((long long)zs[c >> 2] * M + ys[(c >> 1) & 1]) * M + xs[c & 1];
+}
+
+// --------------------------------------------------------------- kernels
+template <typename R>
+__global__ void k_paint_weights(AdjState<R> s, const R* __restrict__ v0, const R* __restrict__ v1,
+                                const R* __restrict__ v2, R* __restrict__ m0, R* __restrict__ m1,
+                                R* __restrict__ m2, int M, long long np) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+    int i[3];
+    unpack3(s.cell[j], i);
+    const R f[3] = {s.fx[j], s.fy[j], s.fz[j]};
+    long long o[8];
+    cic_offsets<R>(i, M, o);
+    const R a = v0[j], b = v1[j], c = v2[j];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const R w = ((k & 1) ? f[0] : R(1) - f[0]) * (((k >> 1) & 1) ? f[1] : R(1) - f[1]) *
+                  ((k >> 2) ? f[2] : R(1) - f[2]);
+      atomicAdd(m0 + o[k], w * a);
+      atomicAdd(m1 + o[k], w * b);
+      atomicAdd(m2 + o[k], w * c);
+    }
+  }
+}
+
+// lam_x += sum_c v_c grad readout(mesh_c) + mass grad readout(phi); optional
+// dot = sum_j lamp_j . readout(mesh)(x_j)
+template <typename R>
+__global__ void k_readout_grad(AdjState<R> s, const R* __restrict__ m0, const R* __restrict__ m1,
+                               const R* __restrict__ m2, const R* __restrict__ v0, const R* __restrict__ v1,
+                               const R* __restrict__ v2, const R* __restrict__ phi, R mass, R* __restrict__ lx,
+                               const R* __restrict__ lp, double* dot, int M, long long np) {
+  double dsum = 0.0;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+    int i[3];
+    unpack3(s.cell[j], i);
+    const R f[3] = {s.fx[j], s.fy[j], s.fz[j]};
+    long long o[8];
+    cic_offsets<R>(i, M, o);
+    const R v[3] = {v0[j], v1[j], v2[j]};
+    R g[3] = {R(0), R(0), R(0)};
+    R val[3] = {R(0), R(0), R(0)};
+    const R* ms[3] = {m0, m1, m2};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
+      const R wx = dx ? f[0] : R(1) - f[0], wy = dy ? f[1] : R(1) - f[1], wz = dz ? f[2] : R(1) - f[2];
+      const R sx = dx ? R(1) : R(-1), sy = dy ? R(1) : R(-1), sz = dz ? R(1) : R(-1);
+      R q = mass * phi[o[k]];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const R mv = ms[c][o[k]];
+        q += v[c] * mv;
+        val[c] += wx * wy * wz * mv;
+      }
+      g[0] += sx * wy * wz * q;
+      g[1] += wx * sy * wz * q;
+      g[2] += wx * wy * sz * q;
+    }
+    lx[j] += g[0];
+    lx[j + np] += g[1];
+    lx[j + 2 * np] += g[2];
+    if (lp) dsum += (double)lp[j] * val[0] + (double)lp[j + np] * val[1] + (double)lp[j + 2 * np] * val[2];
+  }
+  if (dot) block_add(dsum, dot);
+}
+
+template <typename R>
+__global__ void k_axpy(R* __restrict__ y, const R* __restrict__ x, R a, long long n) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    y[j] += a * x[j];
+}
+
+template <typename R>
+__global__ void k_scale(R* __restrict__ y, const R* __restrict__ x, R a, long long n) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    y[j] = a * x[j];
+}
+
+template <typename R>
+__global__ void k_dot(const R* __restrict__ a, const R* __restrict__ b, long long n, double* acc) {
+  double s = 0.0;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    s += (double)a[j] * (double)b[j];
+  block_add(s, acc);
+}
+
+__global__ void k_dsum(const double* __restrict__ a, long long n, double* acc) {
+  double s = 0.0;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+    s += a[j];
+  block_add(s, acc);
+}
+
+// out_c = scale * (ca * lam_x_c + cb * lam_p_c) on the lattice (particle j = lattice j)
+template <typename R>
+__global__ void k_combine2(const R* __restrict__ lx, const R* __restrict__ lp, R* __restrict__ o0,
+                           R* __restrict__ o1, R* __restrict__ o2, double ca, double cb, double scale, long long n) {
+  R* outs[3] = {o0, o1, o2};
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) outs[c][j] = (R)(scale * (ca * (double)lx[j + c * n] + cb * (double)lp[j + c * n]));
+}
+
+// sum_j lam_x . (M/L)(d1 psi1 + d2 psi2) + lam_p . (M/L)(g1 psi1 + g2 psi2)
+template <typename R>
+__global__ void k_ic_dot(const R* __restrict__ lx, const R* __restrict__ lp, const R* __restrict__ a0,
+                         const R* __restrict__ a1, const R* __restrict__ a2, const R* __restrict__ b0,
+                         const R* __restrict__ b1, const R* __restrict__ b2, double d1, double d2, double g1,
+                         double g2, double cpl, long long n, double* acc) {
+  double s = 0.0;
+  const R* A[3] = {a0, a1, a2};
+  const R* B[3] = {b0, b1, b2};
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const double p1 = A[c][j], p2 = B[c] ? (double)B[c][j] : 0.0;
+      s += cpl * ((double)lx[j + c * n] * (d1 * p1 + d2 * p2) + (double)lp[j + c * n] * (g1 * p1 + g2 * p2));
+    }
+  block_add(s, acc);
+}
+
+// cotangents of the six second-derivative fields of the 2LPT source
+template <typename R>
+__global__ void k_lpt2_src_adj(const R* __restrict__ ls, const R* __restrict__ d00, const R* __restrict__ d11,
+                               const R* __restrict__ d22, const R* __restrict__ d01, const R* __restrict__ d02,
+                               const R* __restrict__ d12, R* __restrict__ o00, R* __restrict__ o11,
+                               R* __restrict__ o22, R* __restrict__ o01, R* __restrict__ o02, R* __restrict__ o12,
+                               long long n) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < n; j += (long long)gridDim.x * blockDim.x) {
+    const R l = ls[j];
+    o00[j] = l * (d11[j] + d22[j]);
+    o11[j] = l * (d00[j] + d22[j]);
+    o22[j] = l * (d00[j] + d11[j]);
+    o01[j] = R(-2) * l * d01[j];
+    o02[j] = R(-2) * l * d02[j];
+    o12[j] = R(-2) * l * d12[j];
+  }
+}
+
+// Transpose of the lightcone projection of one shell (mirrors k_lens).
+// Adds d/dx, d/dp (cells) to lam_x, lam_p and writes d/dS (cells) to vS.
+template <typename R>
+__global__ void __launch_bounds__(256) k_lens_vjp(const LensAdjArgs<R> A) {
+  const R cell_len = (R)A.cell_len, lo2 = (R)A.chi_lo2, hi2 = (R)A.chi_hi2;
+  const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
+  const R tan_half = (R)A.tan_half, margin = (R)A.margin;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.np;
+       j += (long long)gridDim.x * blockDim.x) {
+    int ci[3];
+    unpack3(A.st.cell[j], ci);
+    const R cf[3] = {A.st.fx[j], A.st.fy[j], A.st.fz[j]};
+    const R cp[3] = {A.st.px[j], A.st.py[j], A.st.pz[j]};
+    R cs[3] = {R(0), R(0), R(0)};
+    bool have_s = false;
+    double gx[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
+    for (int q = 0; q < A.nrep; ++q) {
+      const Replica rp = A.rep[q];
+      R r[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int ax = rp.perm[d];
+        int i = ci[ax];
+        R f = cf[ax];
+        if (rp.flip >> d & 1) {
+          if (f > R(0)) { i = A.M - 1 - i; f = R(1) - f; }
+          else { i = i == 0 ? 0 : A.M - i; }
+        }
+        i += rp.shift[d];
+        if (i >= A.M) i -= A.M;
+        r[d] = ((R)(i + rp.n[d] * A.M) + f) * cell_len;
+      }
+      const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+      if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) continue;
+      const R lim = r[2] * tan_half + margin;
+      if (fabs(r[0]) > lim || fabs(r[1]) > lim) continue;
+      if (A.S0 && !have_s) {
+        const R* Sm[3] = {A.S0, A.S1, A.S2};
+        long long o[8];
+        cic_offsets<R>(ci, A.M, o);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          R acc = R(0);
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            acc += ((k & 1) ? cf[0] : R(1) - cf[0]) * (((k >> 1) & 1) ? cf[1] : R(1) - cf[1]) *
+                   ((k >> 2) ? cf[2] : R(1) - cf[2]) * Sm[c][o[k]];
+          cs[c] = acc;
+        }
+        have_s = true;
+      }
+      R pr[3], sr[3], sg[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        sg[d] = (rp.flip >> d & 1) ? R(-1) : R(1);
+        pr[d] = sg[d] * cp[rp.perm[d]];
+        sr[d] = sg[d] * cs[rp.perm[d]];
+      }
+      const R chi = sqrt(chi2);
+      R rc[3] = {r[0], r[1], r[2]};
+      R dt = R(0), ddt = R(0);
+      if (A.sub) {
+        const double t = interp_t(A.tab_d1, A.tab_n, A.tab_hinv, (double)chi);
+        dt = (R)((t - A.d1_next) * A.inv_gp_half);
+        ddt = (R)(interp_t(A.tab_dd1, A.tab_n, A.tab_hinv, (double)chi) * A.inv_gp_half);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) rc[d] += pr[d] * dt * cell_len;
+      }
+      if (A.S0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) rc[d] += sr[d] * cell_len;
+      }
+      if (!(rc[2] > R(0))) continue;
+      const R chic = sqrt(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]);
+      const R inz = R(1) / rc[2];
+      const R u = (rc[0] * inz + fov_half) * inv_dth - R(0.5);
+      const R v = (rc[1] * inz + fov_half) * inv_dth - R(0.5);
+      if (!isfinite(u) || !isfinite(v)) continue;
+      if (u < R(-1) || v < R(-1) || u >= (R)A.npix || v >= (R)A.npix) continue;
+      const R fu0 = floor(u), fv0 = floor(v);
+      const int iu = (int)fu0, iv = (int)fv0;
+      const R fu = u - fu0, fv = v - fv0;
+      const double cd = (double)chic;
+      const double inva = interp_t(A.tab_inva, A.tab_n, A.tab_hinv, cd);
+      const double dinva = interp_t(A.tab_dinva, A.tab_n, A.tab_hinv, cd);
+      double grc[3] = {0, 0, 0};
+      for (int s = 0; s < A.nzs; ++s) {
+        const double csd = A.chi_s[s];
+        if (!(cd < csd)) continue;
+        const double fr = 1.0 / cd - 1.0 / csd;
+        const double w = A.wpref * fr * inva;
+        const double dw = A.wpref * (-inva / (cd * cd) + fr * dinva);
+        const double* lam = A.lam + (long long)s * A.npix * A.npix;
+        double Lw = 0, Lu = 0, Lv = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int du = k & 1, dv = k >> 1;
+          const int jx = iu + du, jy = iv + dv;
+          if (jx < 0 || jx >= A.npix || jy < 0 || jy >= A.npix) continue;
+          const double l = lam[(long long)jy * A.npix + jx];
+          const double wu = du ? fu : 1.0 - fu, wv = dv ? fv : 1.0 - fv;
+          Lw += l * wu * wv;
+          Lu += l * (du ? 1.0 : -1.0) * wv;
+          Lv += l * wu * (dv ? 1.0 : -1.0);
+        }
+        const double rad = dw * Lw / cd;
+        const double gu = w * Lu * (double)inv_dth, gv = w * Lv * (double)inv_dth;
+        grc[0] += rad * rc[0] + gu / rc[2];
+        grc[1] += rad * rc[1] + gv / rc[2];
+        grc[2] += rad * rc[2] - (gu * rc[0] + gv * rc[1]) / ((double)rc[2] * rc[2]);
+      }
+      // rc = r + pr dt(|r|) L_cell + sr L_cell
+      double gr[3] = {grc[0], grc[1], grc[2]};
+      if (A.sub) {
+        const double gdp = (grc[0] * pr[0] + grc[1] * pr[1] + grc[2] * pr[2]) * (double)cell_len * ddt / chi;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) gr[d] += gdp * r[d];
+      }
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const int ax = rp.perm[d];
+        gx[ax] += sg[d] * gr[d] * cell_len;
+        if (A.sub) gp[ax] += sg[d] * grc[d] * dt * cell_len;
+        gs[ax] += sg[d] * grc[d] * cell_len;
+      }
+    }
+    A.lx[j] += (R)gx[0];
+    A.lx[j + A.np] += (R)gx[1];
+    A.lx[j + 2 * A.np] += (R)gx[2];
+    A.lp[j] += (R)gp[0];
+    A.lp[j + A.np] += (R)gp[1];
+    A.lp[j + 2 * A.np] += (R)gp[2];
+    if (A.vS) {
+      A.vS[j] += (R)gs[0];
+      A.vS[j + A.np] += (R)gs[1];
+      A.vS[j + 2 * A.np] += (R)gs[2];
+    }
+  }
+}
+
+}  // namespace
+
+// -------------------------------------------------------------- launchers
+static int blocks_for(long long n) {
+  long long b = (n + 255) / 256;
+  return (int)std::min<long long>(std::max<long long>(b, 1), 152LL * 16);
+}
+
+template <typename R>
+void adj_paint_weights(const AdjState<R>& s, const R* v, R* const* meshes, int M, long long np, cudaStream_t st,
+                       Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, np * (4.0 + 6.0 * sizeof(R)) + 3.0 * (double)M * M * M * sizeof(R));
+  k_paint_weights<R><<<blocks_for(np), 256, 0, st>>>(s, v, v + np, v + 2 * np, meshes[0], meshes[1], meshes[2], M, np);
+}
+
+template <typename R>
+void adj_readout_grad(const AdjState<R>& s, R* const* meshes, const R* v, const R* phi, double mass, R* lx,
+                      const R* lp, double* dot, int M, long long np, cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, np * (4.0 + 12.0 * sizeof(R)) + 4.0 * (double)M * M * M * sizeof(R));
+  k_readout_grad<R><<<blocks_for(np), 256, 0, st>>>(s, meshes[0], meshes[1], meshes[2], v, v + np, v + 2 * np, phi,
+                                                   (R)mass, lx, lp, dot, M, np);
+}
+
+template <typename R>
+void adj_axpy(R* y, const R* x, double a, long long n, cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, 3.0 * n * sizeof(R));
+  k_axpy<R><<<blocks_for(n), 256, 0, st>>>(y, x, (R)a, n);
+}
+
+template <typename R>
+void adj_scale(R* y, const R* x, double a, long long n, cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, 2.0 * n * sizeof(R));
+  k_scale<R><<<blocks_for(n), 256, 0, st>>>(y, x, (R)a, n);
+}
+
+template <typename R>
+void adj_dot(const R* a, const R* b, long long n, double* acc, cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, 2.0 * n * sizeof(R));
+  k_dot<R><<<blocks_for(n), 256, 0, st>>>(a, b, n, acc);
+}
+
+void adj_dsum(const double* a, long long n, double* acc, cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, 8.0 * n);
+  k_dsum<<<blocks_for(n), 256, 0, st>>>(a, n, acc);
+}
+
+template <typename R>
+void adj_combine2(const R* lx, const R* lp, R* const* outs, double ca, double cb, double scale, long long n,
+                  cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, 9.0 * n * sizeof(R));
+  k_combine2<R><<<blocks_for(n), 256, 0, st>>>(lx, lp, outs[0], outs[1], outs[2], ca, cb, scale, n);
+}
+
+template <typename R>
+void adj_ic_dot(const R* lx, const R* lp, R* const* psi1, R* const* psi2, double d1, double d2, double g1, double g2,
+                double cpl, long long n, double* acc, cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, 12.0 * n * sizeof(R));
+  k_ic_dot<R><<<blocks_for(n), 256, 0, st>>>(lx, lp, psi1[0], psi1[1], psi1[2], psi2 ? psi2[0] : nullptr,
+                                             psi2 ? psi2[1] : nullptr, psi2 ? psi2[2] : nullptr, d1, d2, g1, g2, cpl,
+                                             n, acc);
+}
+
+template <typename R>
+void adj_lpt2_src(const R* ls, R* const* d, R* const* out, long long n, cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, 13.0 * n * sizeof(R));
+  k_lpt2_src_adj<R><<<blocks_for(n), 256, 0, st>>>(ls, d[0], d[1], d[2], d[3], d[4], d[5], out[0], out[1], out[2],
+                                                   out[3], out[4], out[5], n);
+}
+
+template <typename R>
+void adj_lens(const LensAdjArgs<R>& A, cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ, st, A.np * (4.0 + 12.0 * sizeof(R)));
+  k_lens_vjp<R><<<(int)std::min<long long>((A.np + 255) / 256, 152LL * 8), 256, 0, st>>>(A);
+}
+
+#define PM_ADJ_INST(R)                                                                                          \
+  template void adj_paint_weights<R>(const AdjState<R>&, const R*, R* const*, int, long long, cudaStream_t,     \
+                                     Prof*);                                                                    \
+  template void adj_readout_grad<R>(const AdjState<R>&, R* const*, const R*, const R*, double, R*, const R*,    \
+                                    double*, int, long long, cudaStream_t, Prof*);                              \
+  template void adj_axpy<R>(R*, const R*, double, long long, cudaStream_t, Prof*);                              \
+  template void adj_scale<R>(R*, const R*, double, long long, cudaStream_t, Prof*);                             \
+  template void adj_dot<R>(const R*, const R*, long long, double*, cudaStream_t, Prof*);                        \
+  template void adj_combine2<R>(const R*, const R*, R* const*, double, double, double, long long, cudaStream_t, \
+                                Prof*);                                                                         \
+  template void adj_ic_dot<R>(const R*, const R*, R* const*, R* const*, double, double, double, double, double, \
+                              long long, double*, cudaStream_t, Prof*);                                         \
+  template void adj_lpt2_src<R>(const R*, R* const*, R* const*, long long, cudaStream_t, Prof*);                \
+  template void adj_lens<R>(const LensAdjArgs<R>&, cudaStream_t, Prof*);
+PM_ADJ_INST(float)
+PM_ADJ_INST(double)
+
+}  // namespace pmlens

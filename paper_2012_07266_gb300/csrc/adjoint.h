@@ -1,0 +1,71 @@
+// Internal declarations of the adjoint kernels (adjoint.cu) and of the
+// transposed spectral pass (fft.cu).
+#pragma once
+
+#include "pm_internal.h"
+
+namespace pmlens {
+
+template <typename R>
+struct AdjState {
+  const uint32_t* cell;
+  const R *fx, *fy, *fz, *px, *py, *pz;
+};
+
+template <typename R>
+struct LensAdjArgs {
+  AdjState<R> st;
+  const R *S0, *S1, *S2;  // PGD displacement meshes (cells), or null
+  long long np;
+  int M;
+  double cell_len, chi_lo2, chi_hi2, fov_half, inv_dtheta, tan_half, margin;
+  int npix, nzs, sub;
+  double chi_s[PM_MAX_ZS];
+  double wpref, d1_next, inv_gp_half, tab_hinv;
+  int tab_n;
+  const double *tab_d1, *tab_dd1, *tab_inva, *tab_dinva;
+  const double* lam;  // dL/dkappa, n_zs * npix^2
+  R* lx;              // d/dx accumulators (cells), 3 * np
+  R* lp;              // d/dp accumulators (cells), 3 * np
+  R* vS;              // d/dS out (cells), 3 * np, or null
+  int nrep;
+  Replica rep[kMaxReplicas];
+};
+
+// sum over nin real inputs of conj(multiplier_{first + c}) * DFT(input_c), then
+// inverse transform into `real_out` (the transpose of spectral_apply's
+// outputs first .. first + nin - 1 for the same SpecParams).
+template <typename R>
+cudaError_t spectral_transpose(R* const* real_in, int nin, int first, void* const* ubufs, void* cbuf, R* real_out,
+                               int n, int P, const SpecParams& sp, cudaStream_t s, Prof* prof);
+
+template <typename R>
+void adj_paint_weights(const AdjState<R>& s, const R* v, R* const* meshes, int M, long long np, cudaStream_t st,
+                       Prof* pf);
+template <typename R>
+void adj_readout_grad(const AdjState<R>& s, R* const* meshes, const R* v, const R* phi, double mass, R* lx,
+                      const R* lp, double* dot, int M, long long np, cudaStream_t st, Prof* pf);
+template <typename R>
+void adj_axpy(R* y, const R* x, double a, long long n, cudaStream_t st, Prof* pf);
+template <typename R>
+void adj_scale(R* y, const R* x, double a, long long n, cudaStream_t st, Prof* pf);
+template <typename R>
+void adj_dot(const R* a, const R* b, long long n, double* acc, cudaStream_t st, Prof* pf);
+void adj_dsum(const double* a, long long n, double* acc, cudaStream_t st, Prof* pf);
+template <typename R>
+void adj_combine2(const R* lx, const R* lp, R* const* outs, double ca, double cb, double scale, long long n,
+                  cudaStream_t st, Prof* pf);
+template <typename R>
+void adj_ic_dot(const R* lx, const R* lp, R* const* psi1, R* const* psi2, double d1, double d2, double g1, double g2,
+                double cpl, long long n, double* acc, cudaStream_t st, Prof* pf);
+template <typename R>
+void adj_lpt2_src(const R* ls, R* const* d, R* const* out, long long n, cudaStream_t st, Prof* pf);
+template <typename R>
+void adj_lens(const LensAdjArgs<R>& A, cudaStream_t st, Prof* pf);
+
+// lens kernel in "dot" mode: acc += sum lam * (this shell's map increment)
+template <typename R>
+cudaError_t launch_lens_dot(pm_ctx* c, const LensShell& sh, int use_pgd, const double* lam, const double* tab_d1,
+                            const double* tab_inva, const double* chi_s, double wpref, double* acc);
+
+}  // namespace pmlens

@@ -6,7 +6,7 @@
 #include <new>
 #include <type_traits>
 
-#include "pm_internal.h"
+#include "adjoint.h"
 
 using namespace pmlens;
 
@@ -64,6 +64,34 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
   const size_t ic_end = L.ic_out + 13 * al(grid);
   L.adj = std::max(step_end, ic_end);
   L.total = L.adj;
+  L.state_bytes = al(np * 4) + 2 * al(3 * np * rs);
+  L.nck = 0;
+  L.nic = 0;
+  if (cfg.ckpt_every > 0) {
+    const int k = cfg.ckpt_every;
+    L.nck = (cfg.nsteps + k - 1) / k;
+    L.nic = 28;
+    size_t a = L.adj;
+    L.adj_noise = a; a += al(grid);
+    L.adj_ckpt = a; a += (size_t)L.nck * L.state_bytes;
+    L.adj_seg = a; a += (size_t)(std::min(k, cfg.nsteps) + 1) * L.state_bytes;
+    L.adj_lx = a; a += al(3 * np * rs);
+    L.adj_lp = a; a += al(3 * np * rs);
+    L.adj_v = a; a += al(3 * np * rs);
+    L.adj_vs = a; a += al(3 * np * rs);
+    L.adj_paint = a; a += 3 * al(mesh);
+    L.adj_ic = a; a += (size_t)L.nic * al(grid);
+    L.tab_dd1 = a; a += al(kChiTab * 8);
+    L.tab_dinva = a; a += al(kChiTab * 8);
+    L.tab_d1p = a; a += al(kChiTab * 8);
+    L.tab_d1m = a; a += al(kChiTab * 8);
+    L.tab_invap = a; a += al(kChiTab * 8);
+    L.tab_invam = a; a += al(kChiTab * 8);
+    L.sqrtp_p = a; a += al((3 * (nc / 2) * (nc / 2) + 1) * 8);
+    L.sqrtp_m = a; a += al((3 * (nc / 2) * (nc / 2) + 1) * 8);
+    L.adj_acc = a; a += al((size_t)(4 * cfg.nsteps + 64) * 8);
+    L.total = a;
+  }
 }
 
 template <typename R>
@@ -115,6 +143,78 @@ void build_tables(pm_ctx* c) {
     }
     c->mean_term[s] = 1.5 * cfg.omega_m / (kCoverH0 * kCoverH0) * acc * hh / 3.0;
   }
+}
+
+// Omega_m +/- h coefficient sets for the finite-difference derivative
+void build_adjoint_tables(pm_ctx* c) {
+  const pm_config& cfg = c->cfg;
+  c->adj_h = 1e-3;
+  const int n = cfg.nsteps;
+  for (int sgn = 0; sgn < 2; ++sgn) {
+    const double om = cfg.omega_m + (sgn == 0 ? c->adj_h : -c->adj_h);
+    Cosmo& co = sgn == 0 ? c->cos_p : c->cos_m;
+    co.init(om, cfg.sigma8, cfg.h, cfg.n_s, cfg.omega_b, cfg.t_cmb);
+    std::vector<double>& kk = sgn == 0 ? c->kick_p : c->kick_m;
+    std::vector<double>& dd = sgn == 0 ? c->drift_p : c->drift_m;
+    std::vector<double>& cs = sgn == 0 ? c->chi_s_p : c->chi_s_m;
+    double* mt = sgn == 0 ? c->mean_p : c->mean_m;
+    kk.resize(n);
+    dd.resize(n);
+    for (int i = 0; i < n; ++i) {
+      const double aprev = i == 0 ? c->a[0] : c->ah[i - 1];
+      kk[i] = (co.gp(c->ah[i]) - co.gp(aprev)) / co.gf(c->a[i]);
+      dd[i] = (co.D1(c->a[i + 1]) - co.D1(c->a[i])) / co.gp(c->ah[i]);
+    }
+    cs.resize(cfg.n_zs);
+    for (int s = 0; s < PM_MAX_ZS; ++s) mt[s] = 0.0;
+    for (int s = 0; s < cfg.n_zs; ++s) {
+      cs[s] = co.chi_a(1.0 / (1.0 + cfg.zs[s]));
+      const int m = 8000;
+      const double hh = cs[s] / m;
+      double acc = 0;
+      for (int q = 0; q <= m; ++q) {
+        const double x = q * hh;
+        acc += (q == 0 || q == m ? 1.0 : (q & 1 ? 4.0 : 2.0)) * x * (cs[s] - x) / (cs[s] * co.a_of_chi(x));
+      }
+      mt[s] = 1.5 * om / (kCoverH0 * kCoverH0) * acc * hh / 3.0;
+    }
+  }
+}
+
+cudaError_t upload_adjoint_tables(pm_ctx* c) {
+  const pm_config& cfg = c->cfg;
+  std::vector<double> dd1(kChiTab), dinva(kChiTab), d1p(kChiTab), d1m(kChiTab), ivp(kChiTab), ivm(kChiTab);
+  for (int k = 0; k < kChiTab; ++k) {
+    const double x = k * c->chi_tab_h;
+    const double a = c->cosmo.a_of_chi(x);
+    dd1[k] = -c->cosmo.gp(a) / (a * kCoverH0);  // dD1(a(chi))/dchi
+    dinva[k] = c->cosmo.E(a) / kCoverH0;        // d(1/a)/dchi
+    const double ap = c->cos_p.a_of_chi(x), am = c->cos_m.a_of_chi(x);
+    d1p[k] = c->cos_p.D1(ap);
+    d1m[k] = c->cos_m.D1(am);
+    ivp[k] = 1.0 / ap;
+    ivm[k] = 1.0 / am;
+  }
+  const int nh = cfg.nc / 2;
+  std::vector<double> sp(3 * nh * nh + 1), sm(3 * nh * nh + 1);
+  const double kf = 2.0 * M_PI / cfg.box, vol = cfg.box * cfg.box * cfg.box;
+  const double ncube = (double)cfg.nc * cfg.nc * cfg.nc;
+  sp[0] = sm[0] = 0.0;
+  for (size_t n2 = 1; n2 < sp.size(); ++n2) {
+    const double k = kf * std::sqrt((double)n2);
+    sp[n2] = std::sqrt(c->cos_p.pk(k) * ncube / vol);
+    sm[n2] = std::sqrt(c->cos_m.pk(k) * ncube / vol);
+  }
+  const std::pair<size_t, std::vector<double>*> up[] = {{c->L.tab_dd1, &dd1}, {c->L.tab_dinva, &dinva},
+                                                        {c->L.tab_d1p, &d1p},  {c->L.tab_d1m, &d1m},
+                                                        {c->L.tab_invap, &ivp}, {c->L.tab_invam, &ivm},
+                                                        {c->L.sqrtp_p, &sp},   {c->L.sqrtp_m, &sm}};
+  for (const auto& u : up) {
+    cudaError_t e = cudaMemcpyAsync(c->ws + u.first, u.second->data(), u.second->size() * 8, cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e) return e;
+  }
+  return cudaStreamSynchronize(c->stream);
 }
 
 cudaError_t upload_tables(pm_ctx* c) {
@@ -315,6 +415,316 @@ __global__ void k_unpad_complex(const typename std::conditional<sizeof(R) == 4, 
   }
 }
 
+pm_status read_flags(pm_ctx* c);
+
+// ---------------------------------------------------------------- adjoint
+// copy the working particle state to / from a packed state block
+cudaError_t save_state(pm_ctx* c, size_t dst) {
+  const size_t np = c->np, r3 = 3 * np * c->rsz;
+  char* d = c->ws + dst;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(d, c->ws + c->L.cell, np * 4, cudaMemcpyDeviceToDevice, c->stream))) return e;
+  if ((e = cudaMemcpyAsync(d + al(np * 4), c->ws + c->L.frac, r3, cudaMemcpyDeviceToDevice, c->stream))) return e;
+  return cudaMemcpyAsync(d + al(np * 4) + al(r3), c->ws + c->L.mom, r3, cudaMemcpyDeviceToDevice, c->stream);
+}
+
+cudaError_t load_state(pm_ctx* c, size_t src) {
+  const size_t np = c->np, r3 = 3 * np * c->rsz;
+  const char* s = c->ws + src;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(c->ws + c->L.cell, s, np * 4, cudaMemcpyDeviceToDevice, c->stream))) return e;
+  if ((e = cudaMemcpyAsync(c->ws + c->L.frac, s + al(np * 4), r3, cudaMemcpyDeviceToDevice, c->stream))) return e;
+  return cudaMemcpyAsync(c->ws + c->L.mom, s + al(np * 4) + al(r3), r3, cudaMemcpyDeviceToDevice, c->stream);
+}
+
+template <typename R>
+AdjState<R> state_view(pm_ctx* c, size_t off) {
+  const size_t np = c->np;
+  const char* b = c->ws + off;
+  AdjState<R> s;
+  s.cell = reinterpret_cast<const uint32_t*>(b);
+  const R* f = reinterpret_cast<const R*>(b + al(np * 4));
+  const R* p = reinterpret_cast<const R*>(b + al(np * 4) + al(3 * np * c->rsz));
+  s.fx = f; s.fy = f + np; s.fz = f + 2 * np;
+  s.px = p; s.py = p + np; s.pz = p + 2 * np;
+  return s;
+}
+
+size_t seg_off(pm_ctx* c, int j) { return c->L.adj_seg + (size_t)j * c->L.state_bytes; }
+size_t ckpt_off(pm_ctx* c, int j) { return c->L.adj_ckpt + (size_t)j * c->L.state_bytes; }
+
+template <typename R>
+cudaError_t force_at_working(pm_ctx* c, bool pgd, double alpha) {
+  R* rho = rp<R>(c, c->L.rho);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, c->stream))) return e;
+  if ((e = launch_paint<R>(c, rho))) return e;
+  return force_from_rho<R>(c, pgd, alpha);
+}
+
+SpecParams force_params(pm_ctx* c, bool pgd, double alpha) {
+  SpecParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  const double m3 = (double)c->M * c->M * c->M;
+  sp.op = pgd ? OP_FORCE_PGD : OP_FORCE;
+  sp.kf = 2.0 * M_PI / c->cfg.box;
+  sp.scale = 1.5 * c->cfg.omega_m * (c->M / c->cfg.box) / m3;
+  sp.pgd_scale = alpha * (c->M / c->cfg.box) / m3;
+  sp.kl = c->cfg.pgd_params[2];
+  sp.ks = c->cfg.pgd_params[3];
+  sp.nexp = c->cfg.pgd_params[4];
+  return sp;
+}
+
+// transpose of the mesh force (or PGD) at the state `st`: lam_x += F^T(v)
+template <typename R>
+cudaError_t mesh_vjp(pm_ctx* c, const AdjState<R>& st, const R* v, bool pgd_part, double alpha, R* const* meshes,
+                     const R* lp_for_dot, double* dot) {
+  cudaStream_t s = c->stream;
+  R* pm[3];
+  for (int q = 0; q < 3; ++q) pm[q] = rp<R>(c, c->L.adj_paint + q * al(c->mesh_elems * c->rsz));
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(pm[0], 0, 3 * al(c->mesh_elems * c->rsz), s))) return e;
+  adj_paint_weights<R>(st, v, pm, c->M, c->np, s, &c->prof);
+  void* ub[6];
+  for (int o = 0; o < 6; ++o) ub[o] = c->ws + c->L.ubuf + o * al(cmesh_bytes(c));
+  R* phi = rp<R>(c, c->L.rho);
+  const SpecParams sp = force_params(c, pgd_part, alpha);
+  if ((e = spectral_transpose<R>(pm, 3, pgd_part ? 3 : 0, ub, c->ws + c->L.cbuf, phi, c->M, c->P, sp, s, &c->prof)))
+    return e;
+  const double mass = std::pow((double)c->M / c->nc, 3.0);
+  adj_readout_grad<R>(st, meshes, v, phi, mass, rp<R>(c, c->L.adj_lx), lp_for_dot, dot, c->M, c->np, s, &c->prof);
+  return cudaGetLastError();
+}
+
+LensShell make_shell(pm_ctx* c, int i, const Cosmo& co) {
+  LensShell sh;
+  const double lo = c->chi_a[i + 1], hi = c->chi_a[i];
+  sh.chi_lo2 = lo * lo;
+  sh.chi_hi2 = hi * hi;
+  sh.d1_next = co.D1(c->a[i + 1]);
+  sh.gp_half = co.gp(c->ah[i]);
+  sh.nrep = 0;
+  return sh;
+}
+
+template <typename R>
+pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_params) {
+  const pm_config& cfg = c->cfg;
+  cudaStream_t s = c->stream;
+  Prof* pf = &c->prof;
+  const long long np = c->np, np3 = 3 * np;
+  const int n = cfg.nsteps, k = cfg.ckpt_every;
+  const long long npix2 = (long long)cfg.map_npix * cfg.map_npix;
+  R* lx = rp<R>(c, c->L.adj_lx);
+  R* lp = rp<R>(c, c->L.adj_lp);
+  R* v = rp<R>(c, c->L.adj_v);
+  R* vS = rp<R>(c, c->L.adj_vs);
+  double* acc = reinterpret_cast<double*>(c->ws + c->L.adj_acc);
+  // acc layout: [0,n) kick dots, [n,2n) drift dots, [2n,3n) lens(+h), [3n,4n) lens(-h),
+  //             4n + s: sum of lam over source s, 4n+16..: IC terms
+  double* acc_ic = acc + 4 * n + 16;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(lx, 0, np3 * c->rsz, s))) return PM_ERR_CUDA;
+  if ((e = cudaMemsetAsync(lp, 0, np3 * c->rsz, s))) return PM_ERR_CUDA;
+  if ((e = cudaMemsetAsync(acc, 0, (size_t)(4 * n + 64) * 8, s))) return PM_ERR_CUDA;
+  for (int q = 0; q < cfg.n_zs; ++q) adj_dsum(lam + q * npix2, npix2, acc + 4 * n + q, s, pf);
+  R* F = rp<R>(c, c->L.fmesh);
+  R* Fm[3] = {F, F + c->mesh_elems, F + 2 * c->mesh_elems};
+  R* S = rp<R>(c, c->L.smesh);
+  R* Sm[3] = {S, S + c->mesh_elems, S + 2 * c->mesh_elems};
+  const double vp = std::pow(cfg.box / c->nc, 3.0);
+  const double dth = cfg.map_fov_deg * M_PI / 180.0 / cfg.map_npix;
+  const double wpref_p = 1.5 * (cfg.omega_m + c->adj_h) / (kCoverH0 * kCoverH0) * vp / (dth * dth);
+  const double wpref_m = 1.5 * (cfg.omega_m - c->adj_h) / (kCoverH0 * kCoverH0) * vp / (dth * dth);
+  const int nck = c->L.nck;
+  for (int seg = nck - 1; seg >= 0; --seg) {
+    const int i0 = seg * k, i1 = std::min(n, i0 + k);
+    // recompute the segment forward from its checkpoint, keeping every state
+    if ((e = load_state(c, ckpt_off(c, seg)))) return PM_ERR_CUDA;
+    if ((e = force_at_working<R>(c, false, 0.0))) return PM_ERR_CUDA;
+    if ((e = save_state(c, seg_off(c, 0)))) return PM_ERR_CUDA;
+    for (int i = i0; i < i1; ++i) {
+      R* rho = rp<R>(c, c->L.rho);
+      if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, s))) return PM_ERR_CUDA;
+      if ((e = launch_kdk_paint<R>(c, rho, c->kick[i], c->drift[i]))) return PM_ERR_CUDA;
+      if ((e = force_from_rho<R>(c, false, 0.0))) return PM_ERR_CUDA;
+      if ((e = save_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
+    }
+    // reverse sweep through the segment
+    for (int i = i1 - 1; i >= i0; --i) {
+      const AdjState<R> st1 = state_view<R>(c, seg_off(c, i - i0 + 1));  // x_{i+1}, p_{i+1/2}
+      if (shell_active(c, i)) {
+        const bool pg = cfg.pgd != 0;
+        if (pg) {
+          if ((e = load_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
+          if ((e = force_at_working<R>(c, true, pgd_alpha(c, i)))) return PM_ERR_CUDA;
+        }
+        LensShell sh = make_shell(c, i, c->cosmo);
+        const std::vector<Replica> reps = shell_replicas(c, std::sqrt(sh.chi_lo2), std::sqrt(sh.chi_hi2));
+        LensAdjArgs<R> A;
+        A.st = st1;
+        A.S0 = pg ? Sm[0] : nullptr;
+        A.S1 = pg ? Sm[1] : nullptr;
+        A.S2 = pg ? Sm[2] : nullptr;
+        A.np = np;
+        A.M = c->M;
+        A.cell_len = cfg.box / c->M;
+        A.chi_lo2 = sh.chi_lo2;
+        A.chi_hi2 = sh.chi_hi2;
+        const double fov = cfg.map_fov_deg * M_PI / 180.0;
+        A.fov_half = 0.5 * fov;
+        A.inv_dtheta = 1.0 / dth;
+        A.tan_half = std::tan(0.5 * fov + dth);
+        A.margin = std::max(0.1 * cfg.box, 10.0);
+        A.npix = cfg.map_npix;
+        A.nzs = cfg.n_zs;
+        A.sub = cfg.sub_evolution;
+        for (int q = 0; q < PM_MAX_ZS; ++q) A.chi_s[q] = q < cfg.n_zs ? c->chi_s[q] : 0.0;
+        A.wpref = 1.5 * cfg.omega_m / (kCoverH0 * kCoverH0) * vp / (dth * dth);
+        A.d1_next = sh.d1_next;
+        A.inv_gp_half = 1.0 / sh.gp_half;
+        A.tab_hinv = 1.0 / c->chi_tab_h;
+        A.tab_n = kChiTab;
+        A.tab_d1 = reinterpret_cast<const double*>(c->ws + c->L.tab_d1);
+        A.tab_dd1 = reinterpret_cast<const double*>(c->ws + c->L.tab_dd1);
+        A.tab_inva = reinterpret_cast<const double*>(c->ws + c->L.tab_inva);
+        A.tab_dinva = reinterpret_cast<const double*>(c->ws + c->L.tab_dinva);
+        A.lam = lam;
+        A.lx = lx;
+        A.lp = lp;
+        A.vS = pg ? vS : nullptr;
+        if (pg && (e = cudaMemsetAsync(vS, 0, np3 * c->rsz, s))) return PM_ERR_CUDA;
+        // the working state holds x_{i+1} for the dot passes
+        if (!pg && (e = load_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
+        LensShell shp = make_shell(c, i, c->cos_p), shm = make_shell(c, i, c->cos_m);
+        for (size_t b = 0; b < reps.size(); b += kMaxReplicas) {
+          A.nrep = (int)std::min<size_t>(kMaxReplicas, reps.size() - b);
+          for (int q = 0; q < A.nrep; ++q) A.rep[q] = reps[b + q];
+          adj_lens<R>(A, s, pf);
+          shp.nrep = shm.nrep = A.nrep;
+          for (int q = 0; q < A.nrep; ++q) shp.rep[q] = shm.rep[q] = A.rep[q];
+          if (launch_lens_dot<R>(c, shp, pg, lam, reinterpret_cast<const double*>(c->ws + c->L.tab_d1p),
+                                 reinterpret_cast<const double*>(c->ws + c->L.tab_invap), c->chi_s_p.data(), wpref_p,
+                                 acc + 2 * n + i))
+            return PM_ERR_CUDA;
+          if (launch_lens_dot<R>(c, shm, pg, lam, reinterpret_cast<const double*>(c->ws + c->L.tab_d1m),
+                                 reinterpret_cast<const double*>(c->ws + c->L.tab_invam), c->chi_s_m.data(), wpref_m,
+                                 acc + 3 * n + i))
+            return PM_ERR_CUDA;
+        }
+        if (pg) {
+          // PGD transpose at x_{i+1} (meshes of S still current)
+          if ((e = mesh_vjp<R>(c, st1, vS, true, pgd_alpha(c, i), Sm, nullptr, nullptr))) return PM_ERR_CUDA;
+        }
+      }
+      // drift x_{i+1} = x_i + drift_i p_{i+1/2}
+      adj_dot<R>(lx, st1.px, np3, acc + n + i, s, pf);
+      adj_axpy<R>(lp, lx, c->drift[i], np3, s, pf);
+      // kick p_{i+1/2} = p_{i-1/2} + kick_i F(x_i)
+      const AdjState<R> st0 = state_view<R>(c, seg_off(c, i - i0));
+      if ((e = load_state(c, seg_off(c, i - i0)))) return PM_ERR_CUDA;
+      if ((e = force_at_working<R>(c, false, 0.0))) return PM_ERR_CUDA;
+      adj_scale<R>(v, lp, c->kick[i], np3, s, pf);
+      if ((e = mesh_vjp<R>(c, st0, v, false, 0.0, Fm, lp, acc + i))) return PM_ERR_CUDA;
+    }
+  }
+  // ------------------------------------------------ initial conditions
+  const long long g = (long long)c->nc * c->nc * c->nc;
+  auto field = [&](int q) { return rp<R>(c, c->L.adj_ic + (size_t)q * al(g * c->rsz)); };
+  // fields: 0-2 Psi1, 3-8 second derivatives, 9 source, 10-12 Psi2, 13-15 lamPsi1, 16-18 lamPsi2,
+  //         19 lamSrc, 20-25 lamDeriv, 26 d/dnoise, 27 spare
+  const bool two = cfg.lpt_order == 2;
+  void* ub[9];
+  for (int o = 0; o < 9; ++o) ub[o] = c->ws + c->L.ic_u + o * al(cgrid_bytes(c));
+  auto lpt_forward = [&](const double* sqrtp) -> cudaError_t {
+    SpecParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.op = two ? OP_LPT2_DERIV : OP_LPT1;
+    sp.kf = 2.0 * M_PI / cfg.box;
+    sp.scale = 1.0 / (double)g;
+    sp.sqrtp = sqrtp;
+    R* outs[9];
+    for (int q = 0; q < 9; ++q) outs[q] = field(q);
+    cudaError_t ee = spectral_apply<R>(rp<R>(c, c->L.adj_noise), c->ws + c->L.ic_cbuf, ub, outs, two ? 9 : 3, c->nc,
+                                       c->Pc, sp, s, pf, KK_ADJ);
+    if (ee || !two) return ee;
+    R* d[6];
+    for (int q = 0; q < 6; ++q) d[q] = field(3 + q);
+    if ((ee = launch_lpt2_source<R>(c, d, field(9), g))) return ee;
+    SpecParams sp2 = sp;
+    sp2.op = OP_GRAD_NEG;
+    R* o2[3] = {field(10), field(11), field(12)};
+    return spectral_apply<R>(field(9), c->ws + c->L.ic_cbuf, ub, o2, 3, c->nc, c->Pc, sp2, s, pf, KK_ADJ);
+  };
+  const double cpl = c->M / cfg.box;
+  const double a0 = c->a[0];
+  const Cosmo& co = c->cosmo;
+  // Omega_m through the initial state: central differences of the LPT displacements
+  for (int sgn = 0; sgn < 2; ++sgn) {
+    const Cosmo& cx = sgn == 0 ? c->cos_p : c->cos_m;
+    if ((e = lpt_forward(reinterpret_cast<const double*>(c->ws + (sgn == 0 ? c->L.sqrtp_p : c->L.sqrtp_m)))))
+      return PM_ERR_CUDA;
+    R* p1[3] = {field(0), field(1), field(2)};
+    R* p2[3] = {field(10), field(11), field(12)};
+    adj_ic_dot<R>(lx, lp, p1, two ? p2 : nullptr, cx.D1(a0), two ? cx.D2(a0) : 0.0, cx.gp(a0),
+                  two ? cx.gp2(a0) : 0.0, cpl, g, acc_ic + sgn, s, pf);
+  }
+  if ((e = lpt_forward(reinterpret_cast<const double*>(c->ws + c->L.sqrtp)))) return PM_ERR_CUDA;
+  R* lpsi1[3] = {field(13), field(14), field(15)};
+  R* lpsi2[3] = {field(16), field(17), field(18)};
+  adj_combine2<R>(lx, lp, lpsi1, co.D1(a0), co.gp(a0), cpl, g, s, pf);
+  for (int q = 0; q < 3; ++q) adj_dot<R>(lpsi1[q], field(q), g, acc_ic + 2, s, pf);
+  SpecParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.kf = 2.0 * M_PI / cfg.box;
+  sp.scale = 1.0 / (double)g;
+  sp.sqrtp = reinterpret_cast<const double*>(c->ws + c->L.sqrtp);
+  R* wbar = field(26);
+  if (!two) {
+    sp.op = OP_LPT1;
+    if ((e = spectral_transpose<R>(lpsi1, 3, 0, ub, c->ws + c->L.ic_cbuf, wbar, c->nc, c->Pc, sp, s, pf)))
+      return PM_ERR_CUDA;
+  } else {
+    adj_combine2<R>(lx, lp, lpsi2, co.D2(a0), co.gp2(a0), cpl, g, s, pf);
+    for (int q = 0; q < 3; ++q) adj_dot<R>(lpsi2[q], field(10 + q), g, acc_ic + 3, s, pf);
+    SpecParams sg = sp;
+    sg.op = OP_GRAD_NEG;
+    if ((e = spectral_transpose<R>(lpsi2, 3, 0, ub, c->ws + c->L.ic_cbuf, field(19), c->nc, c->Pc, sg, s, pf)))
+      return PM_ERR_CUDA;
+    R* d[6];
+    R* ld[6];
+    for (int q = 0; q < 6; ++q) { d[q] = field(3 + q); ld[q] = field(20 + q); }
+    adj_lpt2_src<R>(field(19), d, ld, g, s, pf);
+    R* ins[9] = {lpsi1[0], lpsi1[1], lpsi1[2], ld[0], ld[1], ld[2], ld[3], ld[4], ld[5]};
+    sp.op = OP_LPT2_DERIV;
+    if ((e = spectral_transpose<R>(ins, 9, 0, ub, c->ws + c->L.ic_cbuf, wbar, c->nc, c->Pc, sp, s, pf)))
+      return PM_ERR_CUDA;
+  }
+  if (d_noise_out && (e = launch_convert_out<R>(wbar, d_noise_out, g, 1.0, s, pf))) return PM_ERR_CUDA;
+  // ------------------------------------------------ host combination
+  std::vector<double> h(4 * n + 64);
+  if (cudaMemcpyAsync(h.data(), acc, h.size() * 8, cudaMemcpyDeviceToHost, s)) return PM_ERR_CUDA;
+  if (cudaStreamSynchronize(s)) return PM_ERR_CUDA;
+  const double hh = c->adj_h, om = cfg.omega_m;
+  double dom = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double dK = (c->kick_p[i] * (om + hh) - c->kick_m[i] * (om - hh)) / (2 * hh);  // d(kick Om)/dOm
+    dom += dK / om * h[i];
+    dom += (c->drift_p[i] - c->drift_m[i]) / (2 * hh) * h[n + i];
+    dom += (h[2 * n + i] - h[3 * n + i]) / (2 * hh);
+  }
+  for (int q = 0; q < cfg.n_zs; ++q) dom -= h[4 * n + q] * (c->mean_p[q] - c->mean_m[q]) / (2 * hh);
+  const double* hic = h.data() + 4 * n + 16;
+  dom += (hic[0] - hic[1]) / (2 * hh);
+  const double ds8 = (hic[2] + (two ? 2.0 * hic[3] : 0.0)) / cfg.sigma8;
+  if (h_params) {
+    h_params[0] = dom;
+    h_params[1] = ds8;
+  }
+  return read_flags(c);
+}
+
 pm_status read_flags(pm_ctx* c) {
   int h = 0;
   if (cudaMemcpyAsync(&h, c->ws + c->L.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) return PM_ERR_CUDA;
@@ -409,8 +819,13 @@ pm_status pm_init(pm_ctx** out, const pm_config* cfg, void* d_workspace, size_t 
   c->projected = -1;
   c->pgd_valid = 0;
   c->ic_done = 0;
+  c->vjp_state_lost = 0;
   build_tables(c);
   if (upload_tables(c) != cudaSuccess) { delete c; return PM_ERR_CUDA; }
+  if (cfg->ckpt_every > 0) {
+    build_adjoint_tables(c);
+    if (upload_adjoint_tables(c) != cudaSuccess) { delete c; return PM_ERR_CUDA; }
+  }
   *out = c;
   return PM_OK;
 }
@@ -421,11 +836,20 @@ pm_status pm_ic(pm_ctx* c, const double* d_noise) {
     return PM_ERR_CUDA;
   pm_status st = PM_DISPATCH(c, do_ic, c, d_noise);
   if (st) return st;
+  if (c->cfg.ckpt_every > 0) {
+    // keep the noise and the initial state for the adjoint
+    const long long g = (long long)c->nc * c->nc * c->nc;
+    cudaError_t e = c->prec == PM_FP64
+                        ? launch_convert_in<double>(d_noise, rp<double>(c, c->L.adj_noise), g, c->stream, &c->prof)
+                        : launch_convert_in<float>(d_noise, rp<float>(c, c->L.adj_noise), g, c->stream, &c->prof);
+    if (e || save_state(c, ckpt_off(c, 0))) return PM_ERR_CUDA;
+  }
   c->ic_done = 1;
   c->next_step = 0;
   c->last_stepped = -1;
   c->projected = -1;
   c->pgd_valid = 0;
+  c->vjp_state_lost = 0;
   return PM_OK;
 }
 
@@ -435,6 +859,10 @@ pm_status pm_step(pm_ctx* c, int32_t i) {
   if (!c->ic_done || i != c->next_step) return PM_ERR_STATE;
   pm_status st = PM_DISPATCH(c, do_step, c, i);
   if (st) return st;
+  const int k = c->cfg.ckpt_every;
+  if (k > 0 && (i + 1) % k == 0 && i + 1 < c->cfg.nsteps) {
+    if (save_state(c, ckpt_off(c, (i + 1) / k))) return PM_ERR_CUDA;
+  }
   c->next_step = i + 1;
   c->last_stepped = i;
   return PM_OK;
@@ -458,9 +886,14 @@ pm_status kappa_maps(pm_ctx* c, double* d_maps) {
 
 pm_status pm_vjp(pm_ctx* c, const double* d_dL_dkappa, double* d_dL_dnoise, double* h_dL_dparams) {
   if (!c || !d_dL_dkappa) return PM_ERR_ARG;
-  (void)d_dL_dnoise;
-  (void)h_dL_dparams;
-  return PM_ERR_UNSUPPORTED;
+  if (c->cfg.ckpt_every <= 0) return PM_ERR_UNSUPPORTED;
+  if (!c->ic_done || c->next_step != c->cfg.nsteps || c->projected != c->cfg.nsteps - 1 || c->vjp_state_lost)
+    return PM_ERR_STATE;
+  pm_status st = PM_DISPATCH(c, do_vjp, c, d_dL_dkappa, d_dL_dnoise, h_dL_dparams);
+  // the reverse sweep reuses the particle arrays: the forward state is gone
+  c->last_stepped = -1;
+  c->vjp_state_lost = 1;
+  return st;
 }
 
 pm_status pm_destroy(pm_ctx* c) {
@@ -503,6 +936,7 @@ pm_status pm_set_particles(pm_ctx* c, const double* d_x, const double* d_p, int3
   c->next_step = next_step;
   c->last_stepped = next_step - 1;
   c->projected = next_step - 2;
+  c->vjp_state_lost = 1;  // no checkpoints of an externally set trajectory
   return PM_OK;
 }
 

@@ -1,4 +1,5 @@
 // Launchers of the 3D FFT passes and of the fused spectral operators.
+#include "adjoint.h"
 #include "fft_impl.cuh"
 
 namespace pmlens {
@@ -13,7 +14,7 @@ struct Launch {
   static constexpr double CB = (double)N * N * (N / 2 + 1) * sizeof(C);
   static size_t smem_x() { return (size_t)(N / 2 + RowTile<R, N>::ROWS * (N / 2 + 1)) * sizeof(C); }
   static size_t smem_cols() { return (size_t)(N + N * ColTile<R, N>::W) * sizeof(C); }
-  static size_t smem_z() { return (size_t)(N + 2 * N * ColTile<R, N>::W) * sizeof(C); }
+  static size_t smem_z() { return (size_t)(N + 2 * N * ZTile<R, N>::W) * sizeof(C); }
   static int ntiles() { return (N / 2 + 1 + ColTile<R, N>::W - 1) / ColTile<R, N>::W; }
 
   static void attrs() {
@@ -24,6 +25,7 @@ struct Launch {
     cudaFuncSetAttribute(k_fft_cols<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols());
     cudaFuncSetAttribute(k_fft_cols<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols());
     cudaFuncSetAttribute(k_zpass_op<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z());
+    cudaFuncSetAttribute(k_zpass_combine<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z());
     done = true;
   }
 
@@ -52,8 +54,29 @@ struct Launch {
   static void zop(const C* in, const OutPtrs& o, int nout, int P, const SpecParams& sp, cudaStream_t s,
                   Prof* pf, int kind) {
     ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_Z_OP, s, (1 + nout) * CB);
-    dim3 g(ntiles(), N);
-    k_zpass_op<R, N><<<g, ColTile<R, N>::THREADS, smem_z(), s>>>(in, o, nout, P, sp);
+    dim3 g((N / 2 + 1 + ZTile<R, N>::W - 1) / ZTile<R, N>::W, N);
+    k_zpass_op<R, N><<<g, ZTile<R, N>::THREADS, smem_z(), s>>>(in, o, nout, P, sp);
+  }
+
+  static cudaError_t transpose(R* const* real_in, int nin, int first, void* const* ubufs, void* cbuf, R* real_out,
+                               int P, const SpecParams& sp, cudaStream_t s, Prof* pf) {
+    attrs();
+    InPtrs ip;
+    for (int i = 0; i < 9; ++i) ip.p[i] = i < nin ? ubufs[i] : nullptr;
+    for (int i = 0; i < nin; ++i) {
+      C* u = reinterpret_cast<C*>(ubufs[i]);
+      x_fwd(real_in[i], u, P, s, pf, KK_ADJ);
+      y(u, P, false, s, pf, KK_ADJ);
+    }
+    C* c = reinterpret_cast<C*>(cbuf);
+    {
+      ProfScope ps(pf, KK_ADJ, s, (nin + 1) * CB);
+      dim3 g((N / 2 + 1 + ZTile<R, N>::W - 1) / ZTile<R, N>::W, N);
+      k_zpass_combine<R, N><<<g, ZTile<R, N>::THREADS, smem_z(), s>>>(ip, nin, first, c, P, sp);
+    }
+    y(c, P, true, s, pf, KK_ADJ);
+    x_inv(c, real_out, P, s, pf, KK_ADJ);
+    return cudaGetLastError();
   }
 
   static cudaError_t r2c(const R* real, void* cplx, int P, cudaStream_t s, Prof* pf) {
@@ -110,6 +133,15 @@ cudaError_t spectral_apply(const R* real_in, void* cbuf, void* const* ubufs, R* 
   PM_FFT_DISPATCH(n, L::apply(real_in, cbuf, ubufs, real_out, nout, P, sp, s, pf, kind));
 }
 
+template <typename R>
+cudaError_t spectral_transpose(R* const* real_in, int nin, int first, void* const* ubufs, void* cbuf, R* real_out,
+                               int n, int P, const SpecParams& sp, cudaStream_t s, Prof* pf) {
+  if (nin < 1 || nin > 9) return cudaErrorInvalidValue;
+  PM_FFT_DISPATCH(n, L::transpose(real_in, nin, first, ubufs, cbuf, real_out, P, sp, s, pf));
+}
+
+template cudaError_t spectral_transpose<PM_REAL>(PM_REAL* const*, int, int, void* const*, void*, PM_REAL*, int, int,
+                                                  const SpecParams&, cudaStream_t, Prof*);
 template cudaError_t fft3d_r2c<PM_REAL>(const PM_REAL*, void*, int, int, cudaStream_t, Prof*);
 template cudaError_t spectral_apply<PM_REAL>(const PM_REAL*, void*, void* const*, PM_REAL* const*, int, int, int,
                                               const SpecParams&, cudaStream_t, Prof*, int);

@@ -117,8 +117,9 @@ template <> struct Plan<1024> { static constexpr int V = 8; using Rad = Radices<
 
 // One Stockham stage over a column of N elements at buf[row * rs + col * cs];
 // T = N / V threads per column, thread t handles V / RAD butterflies.
-template <typename C, int N, int V, int RAD, bool INV, int NS>
-__device__ __forceinline__ void stage(C* buf, int rs, int cs, int col, int t, const C* tw) {
+template <typename C, int N, int V, int RAD, bool INV, int NS, int RS, int CS>
+__device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
+  constexpr int rs = RS, cs = CS;
   constexpr int T = N / V;
   constexpr int NB = V / RAD;
   constexpr int NR = N / RAD;
@@ -151,22 +152,22 @@ __device__ __forceinline__ void stage(C* buf, int rs, int cs, int col, int t, co
   __syncthreads();
 }
 
-template <typename C, int N, int V, bool INV, int NS, int RAD, int... Rest>
-__device__ __forceinline__ void run_stages(C* buf, int rs, int cs, int col, int t, const C* tw) {
-  stage<C, N, V, RAD, INV, NS>(buf, rs, cs, col, t, tw);
-  if constexpr (sizeof...(Rest) > 0) run_stages<C, N, V, INV, NS * RAD, Rest...>(buf, rs, cs, col, t, tw);
+template <typename C, int N, int V, bool INV, int RS, int CS, int NS, int RAD, int... Rest>
+__device__ __forceinline__ void run_stages(C* buf, int col, int t, const C* tw) {
+  stage<C, N, V, RAD, INV, NS, RS, CS>(buf, col, t, tw);
+  if constexpr (sizeof...(Rest) > 0) run_stages<C, N, V, INV, RS, CS, NS * RAD, Rest...>(buf, col, t, tw);
 }
 
-template <typename C, int N, bool INV, int... Rs>
-__device__ __forceinline__ void fft_column_impl(Radices<Rs...>, C* buf, int rs, int cs, int col, int t,
-                                                const C* tw) {
-  run_stages<C, N, Plan<N>::V, INV, 1, Rs...>(buf, rs, cs, col, t, tw);
+template <typename C, int N, bool INV, int RS, int CS, int... Rs>
+__device__ __forceinline__ void fft_column_impl(Radices<Rs...>, C* buf, int col, int t, const C* tw) {
+  run_stages<C, N, Plan<N>::V, INV, RS, CS, 1, Rs...>(buf, col, t, tw);
 }
 
-// In-place FFT of one column of length N held in shared memory.
-template <typename C, int N, bool INV>
-__device__ __forceinline__ void fft_column(C* buf, int rs, int cs, int col, int t, const C* tw) {
-  fft_column_impl<C, N, INV>(typename Plan<N>::Rad{}, buf, rs, cs, col, t, tw);
+// In-place FFT of one column of length N held in shared memory: element k of
+// column `col` at buf[k * RS + col * CS] (compile-time strides).
+template <typename C, int N, bool INV, int RS, int CS>
+__device__ __forceinline__ void fft_column(C* buf, int col, int t, const C* tw) {
+  fft_column_impl<C, N, INV, RS, CS>(typename Plan<N>::Rad{}, buf, col, t, tw);
 }
 
 // tw[m] = exp(-2 pi i m / N), m < N
@@ -186,6 +187,13 @@ template <typename R, int N> struct ColTile {
   static constexpr int cap_thr = 1024 * Plan<N>::V / N;
   static constexpr int cap = cap_smem < cap_thr ? (cap_smem < 32 ? cap_smem : 32) : (cap_thr < 32 ? cap_thr : 32);
   static constexpr int W = cap >= 32 ? 32 : cap >= 16 ? 16 : cap >= 8 ? 8 : cap >= 4 ? 4 : cap >= 2 ? 2 : 1;
+  static constexpr int THREADS = W * (N / Plan<N>::V);
+};
+
+// fused z pass: half the column tile of the plain passes for large N, so that
+// two blocks (two A/B buffer pairs) share an SM and overlap load and compute
+template <typename R, int N> struct ZTile {
+  static constexpr int W = (N >= 256 && ColTile<R, N>::W >= 2) ? ColTile<R, N>::W / 2 : ColTile<R, N>::W;
   static constexpr int THREADS = W * (N / Plan<N>::V);
 };
 
@@ -215,7 +223,7 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   }
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
-  fft_column<C, H, false>(buf, 1, LD, h, t, tw);
+  fft_column<C, H, false, 1, LD>(buf, h, t, tw);
   for (int e = threadIdx.x; e < ROWS * (H + 1); e += blockDim.x) {
     const int hh = e / (H + 1), k = e - hh * (H + 1);
     const C zk = buf[hh * LD + (k % H)];
@@ -253,7 +261,7 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
   }
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
-  fft_column<C, H, true>(buf, 1, LD, h, t, tw);
+  fft_column<C, H, true, 1, LD>(buf, h, t, tw);
   C* outc = reinterpret_cast<C*>(out);
   for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
     const int hh = e / H, m = e - hh * H;
@@ -280,7 +288,7 @@ k_fft_cols(typename CT<R>::T* __restrict__ data, long long plane_stride, long lo
   }
   __syncthreads();
   const int col = threadIdx.x % W, t = threadIdx.x / W;
-  fft_column<C, N, INV>(buf, W, 1, col, t, tw);
+  fft_column<C, N, INV, W, 1>(buf, col, t, tw);
   for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
     const int row = e / W, c = e - row * W;
     if (c < nv) base[row * row_stride + c] = buf[e];
@@ -289,11 +297,9 @@ k_fft_cols(typename CT<R>::T* __restrict__ data, long long plane_stride, long lo
 
 struct OutPtrs { void* p[9]; };
 
-// Fourier-space operator for output o at integer frequencies (fx, fy, fz).
+// Fourier-space operator of output o at integer frequencies: multiplier re + i im.
 template <typename R>
-__device__ __forceinline__ typename CT<R>::T spec_mult(const SpecParams& sp, int o, int ix, int iy, int iz,
-                                                       int n, typename CT<R>::T a) {
-  using C = typename CT<R>::T;
+__device__ __forceinline__ void spec_coef(const SpecParams& sp, int o, int ix, int iy, int iz, int n, R& re, R& im) {
   const int h = n / 2;
   const int fx = ix <= h ? ix : ix - n, fy = iy <= h ? iy : iy - n, fz = iz <= h ? iz : iz - n;
   const R kf = (R)sp.kf;
@@ -302,7 +308,8 @@ __device__ __forceinline__ typename CT<R>::T spec_mult(const SpecParams& sp, int
   const R inv = k2 > R(0) ? R(1) / k2 : R(0);
   // odd factors vanish on their axis' Nyquist plane
   const R ox = ix == h ? R(0) : kx, oy = iy == h ? R(0) : ky, oz = iz == h ? R(0) : kz;
-  R re = 0, im = 0;  // multiplier = re + i im
+  re = 0;
+  im = 0;
   switch (sp.op) {
     case OP_FORCE:
     case OP_FORCE_PGD: {
@@ -344,15 +351,23 @@ __device__ __forceinline__ typename CT<R>::T spec_mult(const SpecParams& sp, int
     default:
       re = (R)sp.scale;
   }
+}
+
+template <typename R>
+__device__ __forceinline__ typename CT<R>::T spec_mult(const SpecParams& sp, int o, int ix, int iy, int iz,
+                                                       int n, typename CT<R>::T a) {
+  using C = typename CT<R>::T;
+  R re, im;
+  spec_coef<R>(sp, o, ix, iy, iz, n, re, im);
   return C{re * a.x - im * a.y, re * a.y + im * a.x};
 }
 
 // fused z pass: forward z FFT, per-output multiplier, inverse z FFT, store.
 template <typename R, int N>
-__global__ void __launch_bounds__(ColTile<R, N>::THREADS)
+__global__ void __launch_bounds__(ZTile<R, N>::THREADS)
 k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int P, SpecParams sp) {
   using C = typename CT<R>::T;
-  constexpr int W = ColTile<R, N>::W;
+  constexpr int W = ZTile<R, N>::W;
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* A = tw + N;
@@ -370,20 +385,103 @@ k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int
   }
   __syncthreads();
   const int col = threadIdx.x % W, t = threadIdx.x / W;
-  fft_column<C, N, false>(A, W, 1, col, t, tw);
+  fft_column<C, N, false, W, 1>(A, col, t, tw);
+  constexpr int THR = ZTile<R, N>::THREADS;
+  constexpr int EPT = N * W / THR;  // elements per thread, fixed across outputs
+  const bool force = sp.op == OP_FORCE || sp.op == OP_FORCE_PGD;
+  R g[EPT], gp[EPT];
+  if (force) {
+    // (3/2) Om / k^2 and alpha O_L O_S / k^2 per element, once for all outputs
+    const R kf = (R)sp.kf;
+    const int h = N / 2;
+#pragma unroll
+    for (int q = 0; q < EPT; ++q) {
+      const int e = threadIdx.x + q * THR;
+      const int row = e / W, c = e - row * W, ix = kx0 + c;
+      const int fx = ix <= h ? ix : ix - N, fy = iy <= h ? iy : iy - N, fz = row <= h ? row : row - N;
+      const R k2 = kf * kf * (R)(fx * fx + fy * fy + fz * fz);
+      const R inv = k2 > R(0) ? R(1) / k2 : R(0);
+      g[q] = (R)sp.scale * inv;
+      gp[q] = R(0);
+      if (sp.op == OP_FORCE_PGD && k2 > R(0))
+        gp[q] = (R)sp.pgd_scale * inv * exp(-(R)(sp.kl * sp.kl) * inv) * exp(-pow(sqrt(k2) / (R)sp.ks, (R)sp.nexp));
+    }
+  }
   for (int o = 0; o < nout; ++o) {
-    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
-      const int row = e / W, c = e - row * W;
-      B[e] = spec_mult<R>(sp, o, kx0 + c, iy, row, N, A[e]);
+    if (force) {
+      const R kf = (R)sp.kf;
+      const int h = N / 2;
+      const int ax = o % 3;
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = threadIdx.x + q * THR;
+        const int row = e / W, c = e - row * W;
+        const int idx = ax == 0 ? kx0 + c : (ax == 1 ? iy : row);
+        const R odd = idx == h ? R(0) : kf * (R)(idx <= h ? idx : idx - N);
+        const R s = (o < 3 ? g[q] : gp[q]) * odd;  // multiplier i * s
+        const C a = A[e];
+        B[e] = C{-s * a.y, s * a.x};
+      }
+    } else {
+      for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+        const int row = e / W, c = e - row * W;
+        B[e] = spec_mult<R>(sp, o, kx0 + c, iy, row, N, A[e]);
+      }
     }
     __syncthreads();
-    fft_column<C, N, true>(B, W, 1, col, t, tw);
+    fft_column<C, N, true, W, 1>(B, col, t, tw);
     C* dst = reinterpret_cast<C*>(outs.p[o]) + plane;
     for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
       const int row = e / W, c = e - row * W;
       if (c < nv) dst[row * rstride + c] = B[e];
     }
     __syncthreads();
+  }
+}
+
+struct InPtrs { const void* p[9]; };
+
+// transposed fused z pass: B = sum_c conj(m_{first+c}(k)) FFT_z(A_c); store IFFT_z(B)
+template <typename R, int N>
+__global__ void __launch_bounds__(ZTile<R, N>::THREADS)
+k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ out, int P, SpecParams sp) {
+  using C = typename CT<R>::T;
+  constexpr int W = ZTile<R, N>::W;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* A = tw + N;
+  C* B = A + N * W;
+  make_twiddles<C, N>(tw);
+  const int ncols = N / 2 + 1;
+  const int kx0 = blockIdx.x * W;
+  const int iy = blockIdx.y;
+  const long long plane = (long long)iy * P + kx0;
+  const long long rstride = (long long)N * P;
+  const int nv = min(W, ncols - kx0);
+  const int col = threadIdx.x % W, t = threadIdx.x / W;
+  for (int e = threadIdx.x; e < N * W; e += blockDim.x) B[e] = C{0, 0};
+  for (int c = 0; c < nin; ++c) {
+    const C* in = reinterpret_cast<const C*>(ins.p[c]);
+    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+      const int row = e / W, cc = e - row * W;
+      A[e] = cc < nv ? in[plane + row * rstride + cc] : C{0, 0};
+    }
+    __syncthreads();
+    fft_column<C, N, false, W, 1>(A, col, t, tw);
+    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+      const int row = e / W, cc = e - row * W;
+      R re, im;
+      spec_coef<R>(sp, first + c, kx0 + cc, iy, row, N, re, im);
+      im = -im;  // conjugate multiplier: the transpose of the real operator
+      const C a = A[e];
+      B[e] = C{B[e].x + re * a.x - im * a.y, B[e].y + re * a.y + im * a.x};
+    }
+    __syncthreads();
+  }
+  fft_column<C, N, true, W, 1>(B, col, t, tw);
+  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+    const int row = e / W, cc = e - row * W;
+    if (cc < nv) out[plane + row * rstride + cc] = B[e];
   }
 }
 

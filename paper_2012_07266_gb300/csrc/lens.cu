@@ -6,9 +6,10 @@
 // PGD meshes) and tested against every replica of the shell.  Geometry runs in
 // the path's precision (FP32 fast path: positions in Mpc/h to ~1e-7 relative),
 // the lensing weights and the map accumulation always in FP64.
+#include <algorithm>
 #include <cmath>
 
-#include "pm_internal.h"
+#include "adjoint.h"
 
 namespace pmlens {
 
@@ -24,6 +25,8 @@ struct LensArgs {
   double cell_len;
   double chi_lo2, chi_hi2;
   double fov_half, inv_dtheta;
+  double tan_half;  // tan of half the field of view plus one pixel
+  double margin;    // bound on the sub-evolution + PGD displacement (Mpc/h)
   int npix, nzs, sub;
   double chi_s[PM_MAX_ZS];
   double wpref;            // (3/2) Om (H0/c)^2 V_p / Omega_pix
@@ -34,11 +37,27 @@ struct LensArgs {
   const double* tab_inva;  // 1 / a(chi)
   double* maps;
   int* flag;
+  const double* lam;  // when set: accumulate sum(lam * increment) into *acc instead of the maps
+  double* acc;
   int nrep;
   Replica rep[kMaxReplicas];
 };
 
 struct MeanTerms { double v[PM_MAX_ZS]; };
+
+// block-wide sum of one double into *acc
+__device__ __forceinline__ void block_sum(double v, double* acc) {
+  __shared__ double red[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) atomicAdd(acc, v);
+  }
+}
 
 __device__ __forceinline__ double interp(const double* __restrict__ t, int n, double hinv, double x) {
   double u = x * hinv;
@@ -67,6 +86,8 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
   const R cell_len = (R)A.cell_len, lo2 = (R)A.chi_lo2, hi2 = (R)A.chi_hi2;
   const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
+  const R tan_half = (R)A.tan_half, margin = (R)A.margin;
+  double dot = 0.0;
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.np;
        j += (long long)gridDim.x * blockDim.x) {
     const uint32_t c = A.cell[j];
@@ -74,11 +95,7 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
     const R cf[3] = {A.fx[j], A.fy[j], A.fz[j]};
     const R cp[3] = {A.px[j], A.py[j], A.pz[j]};
     R cs[3] = {R(0), R(0), R(0)};
-    if (A.S0) {
-      cs[0] = gather3(A.S0, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
-      cs[1] = gather3(A.S1, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
-      cs[2] = gather3(A.S2, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
-    }
+    bool have_s = false;  // PGD displacement gathered only for particles that may land on the map
     for (int q = 0; q < A.nrep; ++q) {
       const Replica rp = A.rep[q];
       R r[3], pr[3], sr[3];
@@ -101,6 +118,17 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
       if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) continue;
+      // outside the field of view by more than the displacement margin: no weight on the map
+      const R lim = r[2] * tan_half + margin;
+      if (fabs(r[0]) > lim || fabs(r[1]) > lim) continue;
+      if (A.S0 && !have_s) {
+        cs[0] = gather3(A.S0, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
+        cs[1] = gather3(A.S1, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
+        cs[2] = gather3(A.S2, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
+        have_s = true;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sr[d] = (rp.flip >> d & 1) ? -cs[rp.perm[d]] : cs[rp.perm[d]];
+      }
       if (A.sub) {
         const double t = interp(A.tab_d1, A.tab_n, A.tab_hinv, (double)sqrt(chi2));
         const R dt = (R)((t - A.d1_next) * A.inv_gp_half) * cell_len;
@@ -131,16 +159,20 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         const double cs_ = A.chi_s[s];
         if (!(cd < cs_)) continue;
         const double w = A.wpref * (cs_ - cd) / (cs_ * cd) * inva;
-        double* m = A.maps + (long long)s * A.npix * A.npix;
+        const long long off = (long long)s * A.npix * A.npix;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int jx = iu + (k & 1), jy = iv + (k >> 1);
-          if (jx >= 0 && jx < A.npix && jy >= 0 && jy < A.npix)
-            atomicAdd(m + (long long)jy * A.npix + jx, w * (double)cw[k]);
+          if (jx >= 0 && jx < A.npix && jy >= 0 && jy < A.npix) {
+            const long long pix = off + (long long)jy * A.npix + jx;
+            if (A.lam) dot += A.lam[pix] * w * (double)cw[k];
+            else atomicAdd(A.maps + pix, w * (double)cw[k]);
+          }
         }
       }
     }
   }
+  if (A.lam) block_sum(dot, A.acc);
 }
 
 __global__ void k_kappa_finalize(const double* __restrict__ maps, double* __restrict__ out, long long npix2, int nzs,
@@ -156,8 +188,41 @@ __global__ void k_kappa_finalize(const double* __restrict__ maps, double* __rest
 }  // namespace
 
 template <typename R>
+static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs<R>& A);
+
+template <typename R>
 cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
   LensArgs<R> A;
+  fill_lens_args<R>(c, sh, use_pgd, A);
+  long long blocks = (c->np + 255) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  // particle state read once (+ three PGD meshes gathered)
+  ProfScope ps(&c->prof, KK_LENS, c->stream,
+               c->np * (4.0 + 6.0 * sizeof(R)) + (use_pgd ? 3.0 * c->mesh_elems * sizeof(R) : 0.0));
+  k_lens<R><<<(int)blocks, 256, 0, c->stream>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_lens_dot(pm_ctx* c, const LensShell& sh, int use_pgd, const double* lam, const double* tab_d1,
+                            const double* tab_inva, const double* chi_s, double wpref, double* acc) {
+  LensArgs<R> A;
+  fill_lens_args<R>(c, sh, use_pgd, A);
+  A.tab_d1 = tab_d1;
+  A.tab_inva = tab_inva;
+  for (int s = 0; s < PM_MAX_ZS; ++s) A.chi_s[s] = s < c->cfg.n_zs ? chi_s[s] : 0.0;
+  A.wpref = wpref;
+  A.lam = lam;
+  A.acc = acc;
+  long long blocks = (c->np + 255) / 256;
+  if (blocks > 152LL * 8) blocks = 152LL * 8;
+  ProfScope ps(&c->prof, KK_ADJ, c->stream, c->np * (4.0 + 6.0 * sizeof(R)));
+  k_lens<R><<<(int)blocks, 256, 0, c->stream>>>(A);
+  return cudaGetLastError();
+}
+
+template <typename R>
+static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs<R>& A) {
   A.cell = reinterpret_cast<const uint32_t*>(c->ws + c->L.cell);
   const R* f = reinterpret_cast<const R*>(c->ws + c->L.frac);
   const R* p = reinterpret_cast<const R*>(c->ws + c->L.mom);
@@ -178,6 +243,8 @@ cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
   const double dth = fov / c->cfg.map_npix;
   A.fov_half = 0.5 * fov;
   A.inv_dtheta = 1.0 / dth;
+  A.tan_half = std::tan(0.5 * fov + dth);
+  A.margin = std::max(0.1 * c->cfg.box, 10.0);
   A.npix = c->cfg.map_npix;
   A.nzs = c->cfg.n_zs;
   for (int s = 0; s < PM_MAX_ZS; ++s) A.chi_s[s] = s < c->cfg.n_zs ? c->chi_s[s] : 0.0;
@@ -192,15 +259,10 @@ cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
   A.tab_inva = reinterpret_cast<const double*>(c->ws + c->L.tab_inva);
   A.maps = reinterpret_cast<double*>(c->ws + c->L.maps);
   A.flag = flags_ptr(c);
+  A.lam = nullptr;
+  A.acc = nullptr;
   A.nrep = sh.nrep;
   for (int q = 0; q < sh.nrep; ++q) A.rep[q] = sh.rep[q];
-  long long blocks = (c->np + 255) / 256;
-  if (blocks > 152LL * 8) blocks = 152LL * 8;
-  // particle state read once (+ three PGD meshes gathered)
-  ProfScope ps(&c->prof, KK_LENS, c->stream,
-               c->np * (4.0 + 6.0 * sizeof(R)) + (use_pgd ? 3.0 * c->mesh_elems * sizeof(R) : 0.0));
-  k_lens<R><<<(int)blocks, 256, 0, c->stream>>>(A);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_kappa_finalize(pm_ctx* c, double* out) {
@@ -217,5 +279,9 @@ cudaError_t launch_kappa_finalize(pm_ctx* c, double* out) {
 
 template cudaError_t launch_lens<float>(pm_ctx*, const LensShell&, int);
 template cudaError_t launch_lens<double>(pm_ctx*, const LensShell&, int);
+template cudaError_t launch_lens_dot<float>(pm_ctx*, const LensShell&, int, const double*, const double*,
+                                            const double*, const double*, double, double*);
+template cudaError_t launch_lens_dot<double>(pm_ctx*, const LensShell&, int, const double*, const double*,
+                                             const double*, const double*, double, double*);
 
 }  // namespace pmlens

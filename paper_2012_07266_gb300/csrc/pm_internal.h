@@ -97,8 +97,12 @@ struct Layout {
   size_t rho, cbuf, ubuf;
   // IC scratch (aliases step scratch)
   size_t ic_real, ic_cbuf, ic_u, ic_out;
-  // adjoint storage
+  // adjoint storage (ckpt_every > 0)
   size_t adj;
+  size_t state_bytes;       // one particle state: cell | frac x3 | mom x3
+  size_t adj_noise, adj_ckpt, adj_seg, adj_lx, adj_lp, adj_v, adj_vs, adj_paint, adj_ic;
+  size_t tab_dd1, tab_dinva, tab_d1p, tab_d1m, tab_invap, tab_invam, sqrtp_p, sqrtp_m, adj_acc;
+  int nck, nic;             // checkpoints, IC adjoint fields
   size_t total;
 };
 
@@ -123,11 +127,17 @@ struct pm_ctx {
   std::vector<double> chi_s;   // source distances
   double chi_tab_max, chi_tab_h;
   double mean_term[PM_MAX_ZS];
+  // Omega_m +/- h copies of the cosmology-dependent coefficients (adjoint)
+  double adj_h;
+  pmlens::Cosmo cos_p, cos_m;
+  std::vector<double> kick_p, kick_m, drift_p, drift_m, chi_s_p, chi_s_m;
+  double mean_p[PM_MAX_ZS], mean_m[PM_MAX_ZS];
   int next_step;     // next pm_step index; -1 before pm_ic
   int last_stepped;  // index of the last pm_step, -1 none
   int projected;     // last projected shell
   int pgd_valid;     // PGD meshes valid for last_stepped
   int ic_done;
+  int vjp_state_lost;  // 1: checkpoints do not describe the current run
   pmlens::Prof prof;
 };
 
