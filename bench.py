@@ -51,6 +51,8 @@ def args_():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nc", type=int, default=None, help="override particles per side (profiling cases)")
     ap.add_argument("--pgd", type=int, default=None, help="override PGD on/off (profiling cases)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the adjoint, FP64 and serving legs")
+    ap.add_argument("--serve-requests", type=int, default=40)
     return ap.parse_args()
 
 
@@ -288,6 +290,7 @@ def run_gpu(a, rank, world, local_rank):
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one FP64 oracle kick-drift step with PM force of {w['nc']}^3 particles on the "
                          f"{w['nmesh']}^3 mesh ({dt:.1f} s), single-threaded numpy"}
+    extra = {} if (a.no_extra or world > 1) else extra_legs(a, w, dev, rank)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == PM_FP32 else "f64", "data": "synthetic",
@@ -296,10 +299,81 @@ def run_gpu(a, rank, world, local_rank):
                        "l2": "inputs larger than L2 (workspace %.1f GB)" % (sim.nbytes / 1e9),
                        "parallelism": f"replicas x{world}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-            "cpu_baseline": cpu, "kernels": kern}
+            "cpu_baseline": cpu, "kernels": kern, **extra}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def extra_legs(a, w, dev, rank):
+    """Forward + adjoint at the same workload, the plain FP64 path, and the
+    serving mix (Poisson arrivals, mixed sizes and cosmologies)."""
+    import torch
+
+    from paper_2012_07266_gb300.api import PM_FP32, PM_FP64, Simulation
+    from pm_inputs import serving_arrivals, white_noise, workload
+    out = {}
+    npart, nsteps = w["nc"] ** 3, w["nsteps"]
+    noise = torch.from_numpy(white_noise(w["nc"], w["noise_seed"] + rank)).to(dev)
+    # forward + reverse-mode derivative (checkpoint every 4 steps)
+    wa = dict(w, ckpt_every=4)
+    stream = torch.cuda.Stream(dev)
+    sim = Simulation(device=dev, stream=stream, precision=PM_FP32, **wa)
+    lam = None
+
+    def fwd_adj():
+        nonlocal lam
+        k = sim.run(noise)
+        lam = k if lam is None else lam
+        sim.vjp(lam)
+
+    fwd_adj()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    reps = 2
+    t_f = t_fa = 0.0
+    for _ in range(reps):
+        e0.record(stream)
+        k = sim.run(noise)
+        e1.record(stream)
+        sim.vjp(lam)
+        e2.record(stream)
+        e2.synchronize()
+        t_f += e0.elapsed_time(e1)
+        t_fa += e0.elapsed_time(e2)
+    t_f, t_fa = t_f / reps, t_fa / reps
+    out["fwd_adjoint"] = {"value": npart * nsteps / (t_fa * 1e-3), "unit": UNIT, "ms_per_step": t_fa,
+                          "forward_ms": t_f, "adjoint_over_forward": (t_fa - t_f) / t_f,
+                          "checkpoint_every": 4, "workspace_gb": sim.nbytes / 1e9}
+    kappa32 = k.clone()
+    del sim
+    torch.cuda.empty_cache()
+    # plain FP64 path, one simulation at a time
+    sim = Simulation(device=dev, stream=stream, precision=PM_FP64, **w)
+    sim.run(noise)
+    e0.record(stream)
+    k64 = sim.run(noise)
+    e1.record(stream)
+    e1.synchronize()
+    t64 = e0.elapsed_time(e1)
+    err = float((kappa32 - k64).norm() / k64.norm())
+    out["plain_fp64"] = {"value": npart * nsteps / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64,
+                         "fp32_speedup": t64 / t_f, "kappa_rel_l2_fp32_vs_fp64": err}
+    del sim
+    torch.cuda.empty_cache()
+    # serving mix: Poisson arrivals at 20/s, meshes 64/128/192 (nc = mesh/2)
+    from paper_2012_07266_gb300.serve import Server, make_requests
+    base = workload("pm64", box=256.0, map_npix=512, map_fov_deg=5.0, pgd=0, lpt_order=1)
+    specs = serving_arrivals(a.serve_requests, rate_hz=20.0, seed=7)
+    warm = make_requests(specs[:3], base)
+    for r in warm:
+        r.t_arrive = 0.0
+    Server(device=dev, max_slots=8).serve(warm)
+    reqs = make_requests(specs, base)
+    st = Server(device=dev, max_slots=8).serve(reqs)
+    out["serve"] = dict(st.summary(), requests=len(reqs), arrival_rate_hz=20.0,
+                        adjoint_fraction=float(np.mean([r.adjoint for r in reqs])),
+                        failed=sum(r.error is not None for r in reqs))
+    return out
 
 
 def read_traffic(kernel, workload):
