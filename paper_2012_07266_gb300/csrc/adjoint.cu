@@ -29,13 +29,14 @@ __device__ __forceinline__ void unpack3(uint32_t c, int* i) {
   i[2] = c >> 20;
 }
 
-__device__ __forceinline__ double interp_t(const double* __restrict__ t, int n, double hinv, double x) {
-  double u = x * hinv;
+template <typename R>
+__device__ __forceinline__ R interp_t(const R* __restrict__ t, int n, R hinv, R x) {
+  const R u = x * hinv;
   int k = (int)u;
   if (k < 0) k = 0;
   if (k > n - 2) k = n - 2;
-  const double f = u - k;
-  return t[k] * (1.0 - f) + t[k + 1] * f;
+  const R f = u - (R)k;
+  return t[k] * (R(1) - f) + t[k + 1] * f;
 }
 
 // block-wide sum of one double into *acc (one atomic per block)
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(256) k_lens_vjp(const LensAdjArgs<R> A) {
     const R cp[3] = {A.st.px[j], A.st.py[j], A.st.pz[j]};
     R cs[3] = {R(0), R(0), R(0)};
     bool have_s = false;
-    double gx[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
+    R gx[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
     for (int q = 0; q < A.nrep; ++q) {
       const Replica rp = A.rep[q];
       R r[3];
@@ -266,9 +267,9 @@ __global__ void __launch_bounds__(256) k_lens_vjp(const LensAdjArgs<R> A) {
       R rc[3] = {r[0], r[1], r[2]};
       R dt = R(0), ddt = R(0);
       if (A.sub) {
-        const double t = interp_t(A.tab_d1, A.tab_n, A.tab_hinv, (double)chi);
-        dt = (R)((t - A.d1_next) * A.inv_gp_half);
-        ddt = (R)(interp_t(A.tab_dd1, A.tab_n, A.tab_hinv, (double)chi) * A.inv_gp_half);
+        const R t = interp_t<R>(A.tab_d1, A.tab_n, (R)A.tab_hinv, chi);
+        dt = (t - (R)A.d1_next) * (R)A.inv_gp_half;
+        ddt = interp_t<R>(A.tab_dd1, A.tab_n, (R)A.tab_hinv, chi) * (R)A.inv_gp_half;
 #pragma unroll
         for (int d = 0; d < 3; ++d) rc[d] += pr[d] * dt * cell_len;
       }
@@ -286,39 +287,39 @@ __global__ void __launch_bounds__(256) k_lens_vjp(const LensAdjArgs<R> A) {
       const R fu0 = floor(u), fv0 = floor(v);
       const int iu = (int)fu0, iv = (int)fv0;
       const R fu = u - fu0, fv = v - fv0;
-      const double cd = (double)chic;
-      const double inva = interp_t(A.tab_inva, A.tab_n, A.tab_hinv, cd);
-      const double dinva = interp_t(A.tab_dinva, A.tab_n, A.tab_hinv, cd);
-      double grc[3] = {0, 0, 0};
+      const R cd = chic;
+      const R inva = interp_t<R>(A.tab_inva, A.tab_n, (R)A.tab_hinv, cd);
+      const R dinva = interp_t<R>(A.tab_dinva, A.tab_n, (R)A.tab_hinv, cd);
+      R grc[3] = {0, 0, 0};
       for (int s = 0; s < A.nzs; ++s) {
-        const double csd = A.chi_s[s];
+        const R csd = (R)A.chi_s[s];
         if (!(cd < csd)) continue;
-        const double fr = 1.0 / cd - 1.0 / csd;
-        const double w = A.wpref * fr * inva;
-        const double dw = A.wpref * (-inva / (cd * cd) + fr * dinva);
-        const double* lam = A.lam + (long long)s * A.npix * A.npix;
-        double Lw = 0, Lu = 0, Lv = 0;
+        const R fr = R(1) / cd - R(1) / csd;
+        const R w = (R)A.wpref * fr * inva;
+        const R dw = (R)A.wpref * (-inva / (cd * cd) + fr * dinva);
+        const double* lam = A.lam + s * A.npix * A.npix;
+        R Lw = 0, Lu = 0, Lv = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int du = k & 1, dv = k >> 1;
           const int jx = iu + du, jy = iv + dv;
           if (jx < 0 || jx >= A.npix || jy < 0 || jy >= A.npix) continue;
-          const double l = lam[(long long)jy * A.npix + jx];
-          const double wu = du ? fu : 1.0 - fu, wv = dv ? fv : 1.0 - fv;
+          const R l = (R)lam[jy * A.npix + jx];
+          const R wu = du ? fu : R(1) - fu, wv = dv ? fv : R(1) - fv;
           Lw += l * wu * wv;
-          Lu += l * (du ? 1.0 : -1.0) * wv;
-          Lv += l * wu * (dv ? 1.0 : -1.0);
+          Lu += l * (du ? R(1) : R(-1)) * wv;
+          Lv += l * wu * (dv ? R(1) : R(-1));
         }
-        const double rad = dw * Lw / cd;
-        const double gu = w * Lu * (double)inv_dth, gv = w * Lv * (double)inv_dth;
+        const R rad = dw * Lw / cd;
+        const R gu = w * Lu * inv_dth, gv = w * Lv * inv_dth;
         grc[0] += rad * rc[0] + gu / rc[2];
         grc[1] += rad * rc[1] + gv / rc[2];
-        grc[2] += rad * rc[2] - (gu * rc[0] + gv * rc[1]) / ((double)rc[2] * rc[2]);
+        grc[2] += rad * rc[2] - (gu * rc[0] + gv * rc[1]) / (rc[2] * rc[2]);
       }
       // rc = r + pr dt(|r|) L_cell + sr L_cell
-      double gr[3] = {grc[0], grc[1], grc[2]};
+      R gr[3] = {grc[0], grc[1], grc[2]};
       if (A.sub) {
-        const double gdp = (grc[0] * pr[0] + grc[1] * pr[1] + grc[2] * pr[2]) * (double)cell_len * ddt / chi;
+        const R gdp = (grc[0] * pr[0] + grc[1] * pr[1] + grc[2] * pr[2]) * cell_len * ddt / chi;
 #pragma unroll
         for (int d = 0; d < 3; ++d) gr[d] += gdp * r[d];
       }
@@ -330,16 +331,16 @@ __global__ void __launch_bounds__(256) k_lens_vjp(const LensAdjArgs<R> A) {
         gs[ax] += sg[d] * grc[d] * cell_len;
       }
     }
-    A.lx[j] += (R)gx[0];
-    A.lx[j + A.np] += (R)gx[1];
-    A.lx[j + 2 * A.np] += (R)gx[2];
-    A.lp[j] += (R)gp[0];
-    A.lp[j + A.np] += (R)gp[1];
-    A.lp[j + 2 * A.np] += (R)gp[2];
+    A.lx[j] += gx[0];
+    A.lx[j + A.np] += gx[1];
+    A.lx[j + 2 * A.np] += gx[2];
+    A.lp[j] += gp[0];
+    A.lp[j + A.np] += gp[1];
+    A.lp[j + 2 * A.np] += gp[2];
     if (A.vS) {
-      A.vS[j] += (R)gs[0];
-      A.vS[j + A.np] += (R)gs[1];
-      A.vS[j + 2 * A.np] += (R)gs[2];
+      A.vS[j] += gs[0];
+      A.vS[j + A.np] += gs[1];
+      A.vS[j + 2 * A.np] += gs[2];
     }
   }
 }

@@ -23,7 +23,7 @@ struct LensAdjArgs {
   double chi_s[PM_MAX_ZS];
   double wpref, d1_next, inv_gp_half, tab_hinv;
   int tab_n;
-  const double *tab_d1, *tab_dd1, *tab_inva, *tab_dinva;
+  const R *tab_d1, *tab_dd1, *tab_inva, *tab_dinva;  // path precision
   const double* lam;  // dL/dkappa, n_zs * npix^2
   R* lx;              // d/dx accumulators (cells), 3 * np
   R* lp;              // d/dp accumulators (cells), 3 * np
@@ -65,7 +65,7 @@ void adj_lens(const LensAdjArgs<R>& A, cudaStream_t st, Prof* pf);
 
 // lens kernel in "dot" mode: acc += sum lam * (this shell's map increment)
 template <typename R>
-cudaError_t launch_lens_dot(pm_ctx* c, const LensShell& sh, int use_pgd, const double* lam, const double* tab_d1,
-                            const double* tab_inva, const double* chi_s, double wpref, double* acc);
+cudaError_t launch_lens_dot(pm_ctx* c, const LensShell& sh, int use_pgd, const double* lam, int tab_d1,
+                            int tab_inva, const double* chi_s, double wpref, double* acc);
 
 }  // namespace pmlens

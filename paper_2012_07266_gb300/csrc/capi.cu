@@ -51,6 +51,7 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
   L.sqrtp = o; o += al((3 * (nc / 2) * (nc / 2) + 1) * 8);
   L.tab_d1 = o; o += al(kChiTab * 8);
   L.tab_inva = o; o += al(kChiTab * 8);
+  L.ftab = o; o += T_COUNT * al(kChiTab * 4);
   L.scratch = o;
   const int nout = cfg.pgd ? 6 : 3;
   L.rho = o;
@@ -75,6 +76,7 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
     L.adj_noise = a; a += al(grid);
     L.adj_ckpt = a; a += (size_t)L.nck * L.state_bytes;
     L.adj_seg = a; a += (size_t)(std::min(k, cfg.nsteps) + 1) * L.state_bytes;
+    L.adj_fseg = a; a += (size_t)(std::min(k, cfg.nsteps) + 1) * 3 * al(mesh);  // force meshes of the segment
     L.adj_lx = a; a += al(3 * np * rs);
     L.adj_lp = a; a += al(3 * np * rs);
     L.adj_v = a; a += al(3 * np * rs);
@@ -143,6 +145,15 @@ void build_tables(pm_ctx* c) {
     }
     c->mean_term[s] = 1.5 * cfg.omega_m / (kCoverH0 * kCoverH0) * acc * hh / 3.0;
   }
+}
+
+// FP32 mirror of a chi table, uploaded beside the FP64 one
+cudaError_t upload_ftab(pm_ctx* c, int id, const std::vector<double>& v) {
+  std::vector<float> f(v.begin(), v.end());
+  cudaError_t e = cudaMemcpyAsync(c->ws + c->L.ftab + id * al(kChiTab * 4), f.data(), f.size() * 4,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e) return e;
+  return cudaStreamSynchronize(c->stream);  // f goes out of scope
 }
 
 // Omega_m +/- h coefficient sets for the finite-difference derivative
@@ -214,6 +225,10 @@ cudaError_t upload_adjoint_tables(pm_ctx* c) {
                                     c->stream);
     if (e) return e;
   }
+  const std::pair<int, std::vector<double>*> fu[] = {{T_DD1, &dd1}, {T_DINVA, &dinva}, {T_D1P, &d1p},
+                                                     {T_D1M, &d1m}, {T_INVAP, &ivp},   {T_INVAM, &ivm}};
+  for (const auto& u : fu)
+    if (cudaError_t e = upload_ftab(c, u.first, *u.second)) return e;
   return cudaStreamSynchronize(c->stream);
 }
 
@@ -236,6 +251,8 @@ cudaError_t upload_tables(pm_ctx* c) {
   if ((e = cudaMemcpyAsync(c->ws + c->L.tab_inva, inva.data(), kChiTab * 8, cudaMemcpyHostToDevice, c->stream))) return e;
   if ((e = cudaMemcpyAsync(c->ws + c->L.sqrtp, sq.data(), sq.size() * 8, cudaMemcpyHostToDevice, c->stream))) return e;
   if ((e = cudaMemsetAsync(c->ws + c->L.flags, 0, 256, c->stream))) return e;
+  if ((e = upload_ftab(c, T_D1, d1t))) return e;
+  if ((e = upload_ftab(c, T_INVA, inva))) return e;
   return cudaStreamSynchronize(c->stream);  // host vectors go out of scope
 }
 
@@ -451,6 +468,17 @@ AdjState<R> state_view(pm_ctx* c, size_t off) {
 }
 
 size_t seg_off(pm_ctx* c, int j) { return c->L.adj_seg + (size_t)j * c->L.state_bytes; }
+size_t fseg_off(pm_ctx* c, int j) { return c->L.adj_fseg + (size_t)j * 3 * al(c->mesh_elems * c->rsz); }
+
+// keep the current force meshes as segment entry j
+cudaError_t save_force(pm_ctx* c, int j) {
+  const size_t m = c->mesh_elems * c->rsz;
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < 3 && !e; ++q)
+    e = cudaMemcpyAsync(c->ws + fseg_off(c, j) + q * al(m), c->ws + c->L.fmesh + q * m, m, cudaMemcpyDeviceToDevice,
+                        c->stream);
+  return e;
+}
 size_t ckpt_off(pm_ctx* c, int j) { return c->L.adj_ckpt + (size_t)j * c->L.state_bytes; }
 
 template <typename R>
@@ -544,12 +572,14 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
     if ((e = load_state(c, ckpt_off(c, seg)))) return PM_ERR_CUDA;
     if ((e = force_at_working<R>(c, false, 0.0))) return PM_ERR_CUDA;
     if ((e = save_state(c, seg_off(c, 0)))) return PM_ERR_CUDA;
+    if ((e = save_force(c, 0))) return PM_ERR_CUDA;
     for (int i = i0; i < i1; ++i) {
       R* rho = rp<R>(c, c->L.rho);
       if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, s))) return PM_ERR_CUDA;
       if ((e = launch_kdk_paint<R>(c, rho, c->kick[i], c->drift[i]))) return PM_ERR_CUDA;
       if ((e = force_from_rho<R>(c, false, 0.0))) return PM_ERR_CUDA;
       if ((e = save_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
+      if (i + 1 < i1 && (e = save_force(c, i - i0 + 1))) return PM_ERR_CUDA;  // F(x_{i+1}) for kick i+1
     }
     // reverse sweep through the segment
     for (int i = i1 - 1; i >= i0; --i) {
@@ -586,10 +616,10 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
         A.inv_gp_half = 1.0 / sh.gp_half;
         A.tab_hinv = 1.0 / c->chi_tab_h;
         A.tab_n = kChiTab;
-        A.tab_d1 = reinterpret_cast<const double*>(c->ws + c->L.tab_d1);
-        A.tab_dd1 = reinterpret_cast<const double*>(c->ws + c->L.tab_dd1);
-        A.tab_inva = reinterpret_cast<const double*>(c->ws + c->L.tab_inva);
-        A.tab_dinva = reinterpret_cast<const double*>(c->ws + c->L.tab_dinva);
+        A.tab_d1 = chi_table<R>(c, T_D1);
+        A.tab_dd1 = chi_table<R>(c, T_DD1);
+        A.tab_inva = chi_table<R>(c, T_INVA);
+        A.tab_dinva = chi_table<R>(c, T_DINVA);
         A.lam = lam;
         A.lx = lx;
         A.lp = lp;
@@ -604,13 +634,9 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
           adj_lens<R>(A, s, pf);
           shp.nrep = shm.nrep = A.nrep;
           for (int q = 0; q < A.nrep; ++q) shp.rep[q] = shm.rep[q] = A.rep[q];
-          if (launch_lens_dot<R>(c, shp, pg, lam, reinterpret_cast<const double*>(c->ws + c->L.tab_d1p),
-                                 reinterpret_cast<const double*>(c->ws + c->L.tab_invap), c->chi_s_p.data(), wpref_p,
-                                 acc + 2 * n + i))
+          if (launch_lens_dot<R>(c, shp, pg, lam, T_D1P, T_INVAP, c->chi_s_p.data(), wpref_p, acc + 2 * n + i))
             return PM_ERR_CUDA;
-          if (launch_lens_dot<R>(c, shm, pg, lam, reinterpret_cast<const double*>(c->ws + c->L.tab_d1m),
-                                 reinterpret_cast<const double*>(c->ws + c->L.tab_invam), c->chi_s_m.data(), wpref_m,
-                                 acc + 3 * n + i))
+          if (launch_lens_dot<R>(c, shm, pg, lam, T_D1M, T_INVAM, c->chi_s_m.data(), wpref_m, acc + 3 * n + i))
             return PM_ERR_CUDA;
         }
         if (pg) {
@@ -623,10 +649,11 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
       adj_axpy<R>(lp, lx, c->drift[i], np3, s, pf);
       // kick p_{i+1/2} = p_{i-1/2} + kick_i F(x_i)
       const AdjState<R> st0 = state_view<R>(c, seg_off(c, i - i0));
-      if ((e = load_state(c, seg_off(c, i - i0)))) return PM_ERR_CUDA;
-      if ((e = force_at_working<R>(c, false, 0.0))) return PM_ERR_CUDA;
+      R* Fi = rp<R>(c, fseg_off(c, i - i0));  // F(x_i), kept by the segment recompute
+      const size_t mstride = al(c->mesh_elems * c->rsz) / c->rsz;
+      R* Fs[3] = {Fi, Fi + mstride, Fi + 2 * mstride};
       adj_scale<R>(v, lp, c->kick[i], np3, s, pf);
-      if ((e = mesh_vjp<R>(c, st0, v, false, 0.0, Fm, lp, acc + i))) return PM_ERR_CUDA;
+      if ((e = mesh_vjp<R>(c, st0, v, false, 0.0, Fs, lp, acc + i))) return PM_ERR_CUDA;
     }
   }
   // ------------------------------------------------ initial conditions

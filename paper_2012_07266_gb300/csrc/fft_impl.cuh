@@ -204,6 +204,72 @@ template <typename R, int N> struct RowTile {  // x pass: rows of N reals, FFT l
   static constexpr int THREADS = ROWS * T;
 };
 
+// ------------------------------------------------------------ tile copies
+// Copy a W-column x N-row tile between global memory (row stride rstride,
+// columns >= nv absent) and shared memory [row][W].  Every thread issues all
+// of its loads before the first shared-memory store, so that each SM keeps
+// enough bytes in flight to cover the HBM latency; FP32 tiles move as
+// 16-byte pairs of complex values.
+template <typename R, int N, int W, int THREADS>
+__device__ __forceinline__ void load_tile(typename CT<R>::T* dst, const typename CT<R>::T* src, long long rstride,
+                                          int nv) {
+  using C = typename CT<R>::T;
+  if constexpr (sizeof(R) == 4 && W % 2 == 0) {
+    constexpr int WP = W / 2, PER = N * WP / THREADS;
+    static_assert(N * WP % THREADS == 0, "tile split");
+    float4 v[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      const int row = e / WP, c = 2 * (e - row * WP);
+      const C* g = src + row * rstride + c;
+      if (c + 1 < nv) v[q] = *reinterpret_cast<const float4*>(g);
+      else if (c < nv) { const C a = g[0]; v[q] = make_float4(a.x, a.y, 0.f, 0.f); }
+      else v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) reinterpret_cast<float4*>(dst)[threadIdx.x + q * THREADS] = v[q];
+  } else {
+    constexpr int PER = N * W / THREADS;
+    static_assert(N * W % THREADS == 0, "tile split");
+    C v[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      const int row = e / W, c = e - row * W;
+      v[q] = c < nv ? src[row * rstride + c] : C{0, 0};
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) dst[threadIdx.x + q * THREADS] = v[q];
+  }
+}
+
+template <typename R, int N, int W, int THREADS>
+__device__ __forceinline__ void store_tile(typename CT<R>::T* dst, const typename CT<R>::T* src, long long rstride,
+                                           int nv) {
+  using C = typename CT<R>::T;
+  if constexpr (sizeof(R) == 4 && W % 2 == 0) {
+    constexpr int WP = W / 2, PER = N * WP / THREADS;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      const int row = e / WP, c = 2 * (e - row * WP);
+      const float4 v = reinterpret_cast<const float4*>(src)[e];
+      C* g = dst + row * rstride + c;
+      if (c + 1 < nv) *reinterpret_cast<float4*>(g) = v;
+      else if (c < nv) g[0] = C{v.x, v.y};
+    }
+  } else {
+    constexpr int PER = N * W / THREADS;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      const int row = e / W, c = e - row * W;
+      if (c < nv) dst[row * rstride + c] = src[e];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- kernels
 // x pass, forward: real rows -> half-spectrum rows
 template <typename R, int N>
@@ -216,10 +282,34 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   C* buf = tw + H;
   make_twiddles<C, H>(tw);
   const long long row0 = (long long)blockIdx.x * ROWS;
-  const C* inc = reinterpret_cast<const C*>(in);
-  for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
-    const int h = e / H, m = e - h * H;
-    buf[h * LD + m] = inc[(row0 + h) * H + m];
+  {
+    // ROWS consecutive rows are contiguous: ROWS * H complex values, read as pairs
+    constexpr int THR = RowTile<R, N>::THREADS;
+    const C* inc = reinterpret_cast<const C*>(in) + row0 * H;
+    if constexpr (sizeof(R) == 4) {
+      constexpr int PER = ROWS * H / 2 / THR;
+      float4 v[PER];
+#pragma unroll
+      for (int q = 0; q < PER; ++q) v[q] = reinterpret_cast<const float4*>(inc)[threadIdx.x + q * THR];
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = 2 * (threadIdx.x + q * THR);
+        const int h = e / H, m = e - h * H;
+        buf[h * LD + m] = C{v[q].x, v[q].y};
+        buf[h * LD + m + 1] = C{v[q].z, v[q].w};
+      }
+    } else {
+      constexpr int PER = ROWS * H / THR;
+      C v[PER];
+#pragma unroll
+      for (int q = 0; q < PER; ++q) v[q] = inc[threadIdx.x + q * THR];
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int e = threadIdx.x + q * THR;
+        const int h = e / H, m = e - h * H;
+        buf[h * LD + m] = v[q];
+      }
+    }
   }
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
@@ -248,10 +338,21 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
   C* buf = tw + H;
   make_twiddles<C, H>(tw);
   const long long row0 = (long long)blockIdx.x * ROWS;
-  for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
+  constexpr int THR = RowTile<R, N>::THREADS, PER = ROWS * H / THR;
+  C vk[PER], vm[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = threadIdx.x + q * THR;
     const int h = e / H, k = e - h * H;
-    const C xk = in[(row0 + h) * P + k];
-    const C xm = cconj(in[(row0 + h) * P + (H - k)]);
+    vk[q] = in[(row0 + h) * P + k];
+    vm[q] = in[(row0 + h) * P + (H - k)];
+  }
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int e = threadIdx.x + q * THR;
+    const int h = e / H, k = e - h * H;
+    const C xk = vk[q];
+    const C xm = cconj(vm[q]);
     const C ev = cadd(xk, xm);
     R s, c;
     if constexpr (sizeof(R) == 4) sincospif(2.0f * (float)k / (float)N, &s, &c);
@@ -282,17 +383,11 @@ k_fft_cols(typename CT<R>::T* __restrict__ data, long long plane_stride, long lo
   const int kx0 = blockIdx.x * W;
   C* base = data + (long long)blockIdx.y * plane_stride + kx0;
   const int nv = min(W, ncols - kx0);
-  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
-    const int row = e / W, c = e - row * W;
-    buf[e] = c < nv ? base[row * row_stride + c] : C{0, 0};
-  }
+  load_tile<R, N, W, ColTile<R, N>::THREADS>(buf, base, row_stride, nv);
   __syncthreads();
   const int col = threadIdx.x % W, t = threadIdx.x / W;
   fft_column<C, N, INV, W, 1>(buf, col, t, tw);
-  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
-    const int row = e / W, c = e - row * W;
-    if (c < nv) base[row * row_stride + c] = buf[e];
-  }
+  store_tile<R, N, W, ColTile<R, N>::THREADS>(base, buf, row_stride, nv);
 }
 
 struct OutPtrs { void* p[9]; };
@@ -379,10 +474,7 @@ k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int
   const long long plane = (long long)iy * P + kx0;
   const long long rstride = (long long)N * P;
   const int nv = min(W, ncols - kx0);
-  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
-    const int row = e / W, c = e - row * W;
-    A[e] = c < nv ? in[plane + row * rstride + c] : C{0, 0};
-  }
+  load_tile<R, N, W, ZTile<R, N>::THREADS>(A, in + plane, rstride, nv);
   __syncthreads();
   const int col = threadIdx.x % W, t = threadIdx.x / W;
   fft_column<C, N, false, W, 1>(A, col, t, tw);
@@ -430,11 +522,7 @@ k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int
     }
     __syncthreads();
     fft_column<C, N, true, W, 1>(B, col, t, tw);
-    C* dst = reinterpret_cast<C*>(outs.p[o]) + plane;
-    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
-      const int row = e / W, c = e - row * W;
-      if (c < nv) dst[row * rstride + c] = B[e];
-    }
+    store_tile<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o]) + plane, B, rstride, nv);
     __syncthreads();
   }
 }
@@ -462,10 +550,7 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
   for (int e = threadIdx.x; e < N * W; e += blockDim.x) B[e] = C{0, 0};
   for (int c = 0; c < nin; ++c) {
     const C* in = reinterpret_cast<const C*>(ins.p[c]);
-    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
-      const int row = e / W, cc = e - row * W;
-      A[e] = cc < nv ? in[plane + row * rstride + cc] : C{0, 0};
-    }
+    load_tile<R, N, W, ZTile<R, N>::THREADS>(A, in + plane, rstride, nv);
     __syncthreads();
     fft_column<C, N, false, W, 1>(A, col, t, tw);
     for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
@@ -479,10 +564,7 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
     __syncthreads();
   }
   fft_column<C, N, true, W, 1>(B, col, t, tw);
-  for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
-    const int row = e / W, cc = e - row * W;
-    if (cc < nv) out[plane + row * rstride + cc] = B[e];
-  }
+  store_tile<R, N, W, ZTile<R, N>::THREADS>(out + plane, B, rstride, nv);
 }
 
 }  // namespace pmlens

@@ -33,8 +33,8 @@ struct LensArgs {
   double d1_next, inv_gp_half;
   double tab_hinv;
   int tab_n;
-  const double* tab_d1;    // D1(a(chi)) on a uniform chi grid
-  const double* tab_inva;  // 1 / a(chi)
+  const R* tab_d1;         // D1(a(chi)) on a uniform chi grid (path precision)
+  const R* tab_inva;       // 1 / a(chi)
   double* maps;
   int* flag;
   const double* lam;  // when set: accumulate sum(lam * increment) into *acc instead of the maps
@@ -59,13 +59,14 @@ __device__ __forceinline__ void block_sum(double v, double* acc) {
   }
 }
 
-__device__ __forceinline__ double interp(const double* __restrict__ t, int n, double hinv, double x) {
-  double u = x * hinv;
+template <typename R>
+__device__ __forceinline__ R interp(const R* __restrict__ t, int n, R hinv, R x) {
+  const R u = x * hinv;
   int k = (int)u;
   if (k < 0) k = 0;
   if (k > n - 2) k = n - 2;
-  const double f = u - k;
-  return t[k] * (1.0 - f) + t[k + 1] * f;
+  const R f = u - (R)k;
+  return t[k] * (R(1) - f) + t[k + 1] * f;
 }
 
 template <typename R>
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
   const R cell_len = (R)A.cell_len, lo2 = (R)A.chi_lo2, hi2 = (R)A.chi_hi2;
   const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
   const R tan_half = (R)A.tan_half, margin = (R)A.margin;
-  double dot = 0.0;
+  R dot = R(0);
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.np;
        j += (long long)gridDim.x * blockDim.x) {
     const uint32_t c = A.cell[j];
@@ -130,8 +131,8 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         for (int d = 0; d < 3; ++d) sr[d] = (rp.flip >> d & 1) ? -cs[rp.perm[d]] : cs[rp.perm[d]];
       }
       if (A.sub) {
-        const double t = interp(A.tab_d1, A.tab_n, A.tab_hinv, (double)sqrt(chi2));
-        const R dt = (R)((t - A.d1_next) * A.inv_gp_half) * cell_len;
+        const R t = interp<R>(A.tab_d1, A.tab_n, (R)A.tab_hinv, sqrt(chi2));
+        const R dt = (t - (R)A.d1_next) * (R)A.inv_gp_half * cell_len;
 #pragma unroll
         for (int d = 0; d < 3; ++d) r[d] += pr[d] * dt;
       }
@@ -152,27 +153,28 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
       const R fu0 = floor(u), fv0 = floor(v);
       const int iu = (int)fu0, iv = (int)fv0;
       const R fu = u - fu0, fv = v - fv0;
-      const double cd = (double)chic;
-      const double inva = interp(A.tab_inva, A.tab_n, A.tab_hinv, cd);
+      // Born weight in the path's precision, map accumulation in FP64
+      const R inva = interp<R>(A.tab_inva, A.tab_n, (R)A.tab_hinv, chic);
       const R cw[4] = {(R(1) - fu) * (R(1) - fv), fu * (R(1) - fv), (R(1) - fu) * fv, fu * fv};
+      const R wk = (R)A.wpref * inva / chic;
       for (int s = 0; s < A.nzs; ++s) {
-        const double cs_ = A.chi_s[s];
-        if (!(cd < cs_)) continue;
-        const double w = A.wpref * (cs_ - cd) / (cs_ * cd) * inva;
-        const long long off = (long long)s * A.npix * A.npix;
+        const R cs_ = (R)A.chi_s[s];
+        if (!(chic < cs_)) continue;
+        const R w = wk * (cs_ - chic) / cs_;
+        const int off = s * A.npix * A.npix;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int jx = iu + (k & 1), jy = iv + (k >> 1);
           if (jx >= 0 && jx < A.npix && jy >= 0 && jy < A.npix) {
-            const long long pix = off + (long long)jy * A.npix + jx;
-            if (A.lam) dot += A.lam[pix] * w * (double)cw[k];
-            else atomicAdd(A.maps + pix, w * (double)cw[k]);
+            const int pix = off + jy * A.npix + jx;
+            if (A.lam) dot += (R)A.lam[pix] * w * cw[k];
+            else atomicAdd(A.maps + pix, (double)(w * cw[k]));
           }
         }
       }
     }
   }
-  if (A.lam) block_sum(dot, A.acc);
+  if (A.lam) block_sum((double)dot, A.acc);
 }
 
 __global__ void k_kappa_finalize(const double* __restrict__ maps, double* __restrict__ out, long long npix2, int nzs,
@@ -204,12 +206,12 @@ cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
 }
 
 template <typename R>
-cudaError_t launch_lens_dot(pm_ctx* c, const LensShell& sh, int use_pgd, const double* lam, const double* tab_d1,
-                            const double* tab_inva, const double* chi_s, double wpref, double* acc) {
+cudaError_t launch_lens_dot(pm_ctx* c, const LensShell& sh, int use_pgd, const double* lam, int tab_d1,
+                            int tab_inva, const double* chi_s, double wpref, double* acc) {
   LensArgs<R> A;
   fill_lens_args<R>(c, sh, use_pgd, A);
-  A.tab_d1 = tab_d1;
-  A.tab_inva = tab_inva;
+  A.tab_d1 = chi_table<R>(c, tab_d1);
+  A.tab_inva = chi_table<R>(c, tab_inva);
   for (int s = 0; s < PM_MAX_ZS; ++s) A.chi_s[s] = s < c->cfg.n_zs ? chi_s[s] : 0.0;
   A.wpref = wpref;
   A.lam = lam;
@@ -255,8 +257,8 @@ static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs
   A.sub = c->cfg.sub_evolution;
   A.tab_hinv = 1.0 / c->chi_tab_h;
   A.tab_n = kChiTab;
-  A.tab_d1 = reinterpret_cast<const double*>(c->ws + c->L.tab_d1);
-  A.tab_inva = reinterpret_cast<const double*>(c->ws + c->L.tab_inva);
+  A.tab_d1 = chi_table<R>(c, T_D1);
+  A.tab_inva = chi_table<R>(c, T_INVA);
   A.maps = reinterpret_cast<double*>(c->ws + c->L.maps);
   A.flag = flags_ptr(c);
   A.lam = nullptr;
@@ -279,9 +281,9 @@ cudaError_t launch_kappa_finalize(pm_ctx* c, double* out) {
 
 template cudaError_t launch_lens<float>(pm_ctx*, const LensShell&, int);
 template cudaError_t launch_lens<double>(pm_ctx*, const LensShell&, int);
-template cudaError_t launch_lens_dot<float>(pm_ctx*, const LensShell&, int, const double*, const double*,
-                                            const double*, const double*, double, double*);
-template cudaError_t launch_lens_dot<double>(pm_ctx*, const LensShell&, int, const double*, const double*,
-                                             const double*, const double*, double, double*);
+template cudaError_t launch_lens_dot<float>(pm_ctx*, const LensShell&, int, const double*, int, int,
+                                            const double*, double, double*);
+template cudaError_t launch_lens_dot<double>(pm_ctx*, const LensShell&, int, const double*, int, int,
+                                             const double*, double, double*);
 
 }  // namespace pmlens

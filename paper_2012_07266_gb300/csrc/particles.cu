@@ -26,6 +26,11 @@ __device__ __forceinline__ int wrapi(long long i, int M) {
   long long r = i % M;
   return (int)(r < 0 ? r + M : r);
 }
+// 32-bit wrap for the per-step carry (|i| far below 2^31)
+__device__ __forceinline__ int wrap32(int i, int M) {
+  int r = i % M;
+  return r < 0 ? r + M : r;
+}
 
 // split a coordinate in cells into (wrapped integer cell, fraction in [0,1))
 template <typename R>
@@ -39,7 +44,7 @@ __device__ __forceinline__ void split_cells(double X, int M, int& i, R& f) {
 }
 
 struct Corners {
-  long long r00, r01, r10, r11;  // row offsets (z, y) of the 4 x-rows
+  unsigned r00, r01, r10, r11;  // row offsets (z, y) of the 4 x-rows (M^3 <= 2^30)
   int x0, x1;
 };
 
@@ -48,10 +53,10 @@ __device__ __forceinline__ Corners corners(int M, int ix, int iy, int iz) {
   const int iy1 = iy + 1 == M ? 0 : iy + 1;
   const int iz1 = iz + 1 == M ? 0 : iz + 1;
   Corners c;
-  c.r00 = ((long long)iz * M + iy) * M;
-  c.r01 = ((long long)iz * M + iy1) * M;
-  c.r10 = ((long long)iz1 * M + iy) * M;
-  c.r11 = ((long long)iz1 * M + iy1) * M;
+  c.r00 = ((unsigned)iz * M + iy) * M;
+  c.r01 = ((unsigned)iz * M + iy1) * M;
+  c.r10 = ((unsigned)iz1 * M + iy) * M;
+  c.r11 = ((unsigned)iz1 * M + iy1) * M;
   c.x0 = ix;
   c.x1 = ix1;
   return c;
@@ -185,9 +190,9 @@ __global__ void k_kdk_paint(PState<R> s, const R* __restrict__ F0, const R* __re
     if (nx >= R(1)) { nx -= R(1); cx += R(1); }
     if (ny >= R(1)) { ny -= R(1); cy += R(1); }
     if (nz >= R(1)) { nz -= R(1); cz += R(1); }
-    ix = wrapi((long long)ix + (long long)cx, M);
-    iy = wrapi((long long)iy + (long long)cy, M);
-    iz = wrapi((long long)iz + (long long)cz, M);
+    ix = wrap32(ix + (int)cx, M);
+    iy = wrap32(iy + (int)cy, M);
+    iz = wrap32(iz + (int)cz, M);
     s.cell[j] = pack(ix, iy, iz);
     s.fx[j] = nx; s.fy[j] = ny; s.fz[j] = nz;
     scatter(rho, corners(M, ix, iy, iz), nx, ny, nz, mass);

@@ -89,6 +89,9 @@ struct ProfScope {
   ~ProfScope();
 };
 
+// chi-grid tables (FP64 in the workspace, FP32 mirrors for the FP32 path)
+enum TabId { T_D1 = 0, T_INVA, T_DD1, T_DINVA, T_D1P, T_D1M, T_INVAP, T_INVAM, T_COUNT };
+
 // workspace layout (byte offsets)
 struct Layout {
   size_t cell, frac, mom, fmesh, smesh, maps, flags, sqrtp, tab_d1, tab_inva;
@@ -100,9 +103,10 @@ struct Layout {
   // adjoint storage (ckpt_every > 0)
   size_t adj;
   size_t state_bytes;       // one particle state: cell | frac x3 | mom x3
-  size_t adj_noise, adj_ckpt, adj_seg, adj_lx, adj_lp, adj_v, adj_vs, adj_paint, adj_ic;
+  size_t adj_noise, adj_ckpt, adj_seg, adj_fseg, adj_lx, adj_lp, adj_v, adj_vs, adj_paint, adj_ic;
   size_t tab_dd1, tab_dinva, tab_d1p, tab_d1m, tab_invap, tab_invam, sqrtp_p, sqrtp_m, adj_acc;
   int nck, nic;             // checkpoints, IC adjoint fields
+  size_t ftab;              // FP32 mirrors of the chi tables (TabId order)
   size_t total;
 };
 
@@ -201,6 +205,27 @@ cudaError_t launch_kappa_finalize(pm_ctx* c, double* out);
 
 // helpers
 inline char* ws_ptr(pm_ctx* c, size_t off) { return c->ws + off; }
+
+// chi table `id` in the path's precision R (FP64 workspace copy or FP32 mirror)
+template <typename R>
+inline const R* chi_table(pm_ctx* c, int id) {
+  if constexpr (sizeof(R) == 8) {
+    size_t off = 0;
+    switch (id) {
+      case T_D1: off = c->L.tab_d1; break;
+      case T_INVA: off = c->L.tab_inva; break;
+      case T_DD1: off = c->L.tab_dd1; break;
+      case T_DINVA: off = c->L.tab_dinva; break;
+      case T_D1P: off = c->L.tab_d1p; break;
+      case T_D1M: off = c->L.tab_d1m; break;
+      case T_INVAP: off = c->L.tab_invap; break;
+      default: off = c->L.tab_invam;
+    }
+    return reinterpret_cast<const R*>(c->ws + off);
+  } else {
+    return reinterpret_cast<const R*>(c->ws + c->L.ftab + (size_t)id * ((kChiTab * 4 + 255) & ~size_t(255)));
+  }
+}
 inline int* flags_ptr(pm_ctx* c) { return reinterpret_cast<int*>(c->ws + c->L.flags); }
 
 }  // namespace pmlens
