@@ -31,6 +31,7 @@ UNITS = [
     ("prof.cpp", "prof.o", []),
     ("static_forces.cu", "static_forces.o", []),
     ("adjoint.cu", "adjoint.o", []),
+    ("sort.cu", "sort.o", []),
 ]
 
 

@@ -44,6 +44,12 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
   L.cell = o; o += al(np * 4);
   L.frac = o; o += al(3 * np * rs);
   L.mom = o; o += al(3 * np * rs);
+  L.pid = o; o += al(np * 4);
+  L.cell2 = o; o += al(np * 4);
+  L.frac2 = o; o += al(3 * np * rs);
+  L.mom2 = o; o += al(3 * np * rs);
+  L.pid2 = o; o += al(np * 4);
+  L.sort_cnt = o; o += al(sort_scratch_bytes((int)M));
   L.fmesh = o; o += al(3 * mesh);
   L.smesh = o; o += cfg.pgd ? al(3 * mesh) : 0;
   L.maps = o; o += al((size_t)cfg.n_zs * cfg.map_npix * cfg.map_npix * 8);
@@ -65,7 +71,7 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
   const size_t ic_end = L.ic_out + 13 * al(grid);
   L.adj = std::max(step_end, ic_end);
   L.total = L.adj;
-  L.state_bytes = al(np * 4) + 2 * al(3 * np * rs);
+  L.state_bytes = 2 * al(np * 4) + 2 * al(3 * np * rs);  // cell | frac | mom | pid
   L.nck = 0;
   L.nic = 0;
   if (cfg.ckpt_every > 0) {
@@ -330,6 +336,7 @@ pm_status do_ic(pm_ctx* c, const double* d_noise) {
   if ((e = launch_ic_particles<R>(c, outs, psi2, co.D1(a0), psi2 ? co.D2(a0) : 0.0, co.gp(a0),
                                   psi2 ? co.gp2(a0) : 0.0)))
     return PM_ERR_CUDA;
+  launch_iota(c);  // lattice order
   R* rho = rp<R>(c, c->L.rho);
   if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, s))) return PM_ERR_CUDA;
   if ((e = launch_paint<R>(c, rho))) return PM_ERR_CUDA;
@@ -442,7 +449,9 @@ cudaError_t save_state(pm_ctx* c, size_t dst) {
   cudaError_t e;
   if ((e = cudaMemcpyAsync(d, c->ws + c->L.cell, np * 4, cudaMemcpyDeviceToDevice, c->stream))) return e;
   if ((e = cudaMemcpyAsync(d + al(np * 4), c->ws + c->L.frac, r3, cudaMemcpyDeviceToDevice, c->stream))) return e;
-  return cudaMemcpyAsync(d + al(np * 4) + al(r3), c->ws + c->L.mom, r3, cudaMemcpyDeviceToDevice, c->stream);
+  if ((e = cudaMemcpyAsync(d + al(np * 4) + al(r3), c->ws + c->L.mom, r3, cudaMemcpyDeviceToDevice, c->stream)))
+    return e;
+  return cudaMemcpyAsync(d + al(np * 4) + 2 * al(r3), c->ws + c->L.pid, np * 4, cudaMemcpyDeviceToDevice, c->stream);
 }
 
 cudaError_t load_state(pm_ctx* c, size_t src) {
@@ -451,7 +460,14 @@ cudaError_t load_state(pm_ctx* c, size_t src) {
   cudaError_t e;
   if ((e = cudaMemcpyAsync(c->ws + c->L.cell, s, np * 4, cudaMemcpyDeviceToDevice, c->stream))) return e;
   if ((e = cudaMemcpyAsync(c->ws + c->L.frac, s + al(np * 4), r3, cudaMemcpyDeviceToDevice, c->stream))) return e;
-  return cudaMemcpyAsync(c->ws + c->L.mom, s + al(np * 4) + al(r3), r3, cudaMemcpyDeviceToDevice, c->stream);
+  if ((e = cudaMemcpyAsync(c->ws + c->L.mom, s + al(np * 4) + al(r3), r3, cudaMemcpyDeviceToDevice, c->stream)))
+    return e;
+  return cudaMemcpyAsync(c->ws + c->L.pid, s + al(np * 4) + 2 * al(r3), np * 4, cudaMemcpyDeviceToDevice, c->stream);
+}
+
+const uint32_t* state_pid(pm_ctx* c, size_t off) {
+  const size_t np = c->np, r3 = 3 * np * c->rsz;
+  return reinterpret_cast<const uint32_t*>(c->ws + off + al(np * 4) + 2 * al(r3));
 }
 
 template <typename R>
@@ -568,6 +584,15 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
   const int nck = c->L.nck;
   for (int seg = nck - 1; seg >= 0; --seg) {
     const int i0 = seg * k, i1 = std::min(n, i0 + k);
+    if (seg < nck - 1) {
+      // the adjoint state is in checkpoint seg+1's particle order; bring it to seg's
+      const uint32_t* pid_next = state_pid(c, ckpt_off(c, seg + 1));
+      const uint32_t* pid_here = state_pid(c, ckpt_off(c, seg));
+      for (R* a : {lx, lp}) {
+        if (launch_unpermute3<R>(c, a, pid_next, v)) return PM_ERR_CUDA;
+        if (launch_permute3<R>(c, v, pid_here, a)) return PM_ERR_CUDA;
+      }
+    }
     // recompute the segment forward from its checkpoint, keeping every state
     if ((e = load_state(c, ckpt_off(c, seg)))) return PM_ERR_CUDA;
     if ((e = force_at_working<R>(c, false, 0.0))) return PM_ERR_CUDA;
@@ -764,6 +789,7 @@ pm_status read_flags(pm_ctx* c) {
 template <typename R>
 pm_status do_set_particles(pm_ctx* c, const double* x, const double* p, int ns) {
   if (launch_set_particles<R>(c, x, p)) return PM_ERR_CUDA;
+  launch_iota(c);
   R* rho = rp<R>(c, c->L.rho);
   if (cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, c->stream)) return PM_ERR_CUDA;
   if (launch_paint<R>(c, rho)) return PM_ERR_CUDA;
@@ -886,6 +912,13 @@ pm_status pm_step(pm_ctx* c, int32_t i) {
   if (!c->ic_done || i != c->next_step) return PM_ERR_STATE;
   pm_status st = PM_DISPATCH(c, do_step, c, i);
   if (st) return st;
+  // restore spatial locality of the particle order (at checkpoint boundaries when the
+  // adjoint is on, so that every checkpoint segment keeps one particle order)
+  const int se = sort_every(c->cfg);
+  if ((i + 1) % se == 0 && i + 1 < c->cfg.nsteps) {
+    cudaError_t e = c->prec == PM_FP64 ? sort_particles<double>(c) : sort_particles<float>(c);
+    if (e) return PM_ERR_CUDA;
+  }
   const int k = c->cfg.ckpt_every;
   if (k > 0 && (i + 1) % k == 0 && i + 1 < c->cfg.nsteps) {
     if (save_state(c, ckpt_off(c, (i + 1) / k))) return PM_ERR_CUDA;

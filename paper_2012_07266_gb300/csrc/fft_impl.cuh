@@ -115,11 +115,19 @@ template <> struct Plan<256> { static constexpr int V = 8; using Rad = Radices<8
 template <> struct Plan<512> { static constexpr int V = 8; using Rad = Radices<8, 8, 8>; };
 template <> struct Plan<1024> { static constexpr int V = 8; using Rad = Radices<8, 8, 8, 2>; };
 
-// One Stockham stage over a column of N elements at buf[row * rs + col * cs];
-// T = N / V threads per column, thread t handles V / RAD butterflies.
+// Element k of a unit-stride column sits at pad(k) = k + k / 16: the first
+// Stockham stage writes 8 consecutive outputs per thread (stride 8 across
+// lanes), which without the pad is a 16-way shared-memory bank conflict.
+__device__ __forceinline__ int pad16(int k) { return k + (k >> 4); }
+template <int H> struct PadLen { static constexpr int value = H + H / 16; };
+
+// One Stockham stage over a column of N elements at buf[row * rs + col * cs]
+// (RS == 1: buf[pad16(row) + col * cs]); T = N / V threads per column, thread
+// t handles V / RAD butterflies.
 template <typename C, int N, int V, int RAD, bool INV, int NS, int RS, int CS>
 __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
-  constexpr int rs = RS, cs = CS;
+  constexpr int cs = CS;
+  auto at = [&](int row) -> C& { return RS == 1 ? buf[pad16(row) + col * cs] : buf[row * RS + col * cs]; };
   constexpr int T = N / V;
   constexpr int NB = V / RAD;
   constexpr int NR = N / RAD;
@@ -129,7 +137,7 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
   for (int b = 0; b < NB; ++b) {
     const int j = t + b * T;
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) v[b][k] = buf[(j + k * NR) * rs + col * cs];
+    for (int k = 0; k < RAD; ++k) v[b][k] = at(j + k * NR);
   }
   __syncthreads();
 #pragma unroll
@@ -147,7 +155,7 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
     dft<RAD, INV>(v[b]);
     const int base = (j - jm) * RAD + jm;
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) buf[(base + k * NS) * rs + col * cs] = v[b][k];
+    for (int k = 0; k < RAD; ++k) at(base + k * NS) = v[b][k];
   }
   __syncthreads();
 }
@@ -276,7 +284,7 @@ template <typename R, int N>
 __global__ void __launch_bounds__(RowTile<R, N>::THREADS)
 k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P) {
   using C = typename CT<R>::T;
-  constexpr int H = N / 2, ROWS = RowTile<R, N>::ROWS, T = RowTile<R, N>::T, LD = H + 1;
+  constexpr int H = N / 2, ROWS = RowTile<R, N>::ROWS, T = RowTile<R, N>::T, LD = PadLen<H>::value + 1;
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + H;
@@ -295,8 +303,8 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
       for (int q = 0; q < PER; ++q) {
         const int e = 2 * (threadIdx.x + q * THR);
         const int h = e / H, m = e - h * H;
-        buf[h * LD + m] = C{v[q].x, v[q].y};
-        buf[h * LD + m + 1] = C{v[q].z, v[q].w};
+        buf[h * LD + pad16(m)] = C{v[q].x, v[q].y};
+        buf[h * LD + pad16(m + 1)] = C{v[q].z, v[q].w};
       }
     } else {
       constexpr int PER = ROWS * H / THR;
@@ -307,7 +315,7 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
       for (int q = 0; q < PER; ++q) {
         const int e = threadIdx.x + q * THR;
         const int h = e / H, m = e - h * H;
-        buf[h * LD + m] = v[q];
+        buf[h * LD + pad16(m)] = v[q];
       }
     }
   }
@@ -316,8 +324,8 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   fft_column<C, H, false, 1, LD>(buf, h, t, tw);
   for (int e = threadIdx.x; e < ROWS * (H + 1); e += blockDim.x) {
     const int hh = e / (H + 1), k = e - hh * (H + 1);
-    const C zk = buf[hh * LD + (k % H)];
-    const C zm = cconj(buf[hh * LD + ((H - k) % H)]);
+    const C zk = buf[hh * LD + pad16(k % H)];
+    const C zm = cconj(buf[hh * LD + pad16((H - k) % H)]);
     const C ev = C{R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y)};
     const C od = C{R(0.5) * (zk.y - zm.y), -R(0.5) * (zk.x - zm.x)};  // (zk - zm) / (2i)
     R s, c;
@@ -332,7 +340,7 @@ template <typename R, int N>
 __global__ void __launch_bounds__(RowTile<R, N>::THREADS)
 k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P) {
   using C = typename CT<R>::T;
-  constexpr int H = N / 2, ROWS = RowTile<R, N>::ROWS, T = RowTile<R, N>::T, LD = H + 1;
+  constexpr int H = N / 2, ROWS = RowTile<R, N>::ROWS, T = RowTile<R, N>::T, LD = PadLen<H>::value + 1;
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + H;
@@ -358,7 +366,7 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
     if constexpr (sizeof(R) == 4) sincospif(2.0f * (float)k / (float)N, &s, &c);
     else sincospi(2.0 * (double)k / (double)N, &s, &c);
     const C od = cmul(C{c, s}, csub(xk, xm));
-    buf[h * LD + k] = C{ev.x - od.y, ev.y + od.x};  // ev + i od
+    buf[h * LD + pad16(k)] = C{ev.x - od.y, ev.y + od.x};  // ev + i od
   }
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
@@ -366,13 +374,13 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
   C* outc = reinterpret_cast<C*>(out);
   for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
     const int hh = e / H, m = e - hh * H;
-    outc[(row0 + hh) * H + m] = buf[hh * LD + m];
+    outc[(row0 + hh) * H + m] = buf[hh * LD + pad16(m)];
   }
 }
 
 // y or z pass in place: column tiles of W kx values over a full axis.
 template <typename R, int N, bool INV>
-__global__ void __launch_bounds__(ColTile<R, N>::THREADS)
+__global__ void __launch_bounds__(ColTile<R, N>::THREADS, 2048 / ColTile<R, N>::THREADS)
 k_fft_cols(typename CT<R>::T* __restrict__ data, long long plane_stride, long long row_stride, int ncols) {
   using C = typename CT<R>::T;
   constexpr int W = ColTile<R, N>::W;

@@ -9,6 +9,7 @@
 #include <cmath>
 
 #include "pm_internal.h"
+#include "warp_agg.cuh"
 
 namespace pmlens {
 
@@ -112,6 +113,23 @@ __device__ __forceinline__ void scatter(R* __restrict__ m, const Corners& c, R f
   atomicAdd(m + c.r11 + c.x1, w11 * fx);
 }
 
+// CIC scatter with warp-aggregated atomics; `valid` false adds nothing
+template <typename R>
+__device__ __forceinline__ void scatter_agg(R* __restrict__ m, const Corners& c, R fx, R fy, R fz, R w, bool valid,
+                                            R* wsm) {
+  const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
+  const R wv = valid ? w : R(0);
+  const R w00 = wv * gz * gy, w01 = wv * gz * fy, w10 = wv * fz * gy, w11 = wv * fz * fy;
+  warp_agg_add(m, c.r00 + c.x0, w00 * gx, wsm);
+  warp_agg_add(m, c.r00 + c.x1, w00 * fx, wsm);
+  warp_agg_add(m, c.r01 + c.x0, w01 * gx, wsm);
+  warp_agg_add(m, c.r01 + c.x1, w01 * fx, wsm);
+  warp_agg_add(m, c.r10 + c.x0, w10 * gx, wsm);
+  warp_agg_add(m, c.r10 + c.x1, w10 * fx, wsm);
+  warp_agg_add(m, c.r11 + c.x0, w11 * gx, wsm);
+  warp_agg_add(m, c.r11 + c.x1, w11 * fx, wsm);
+}
+
 template <typename R>
 struct PState {
   uint32_t* cell;
@@ -161,28 +179,40 @@ __global__ void k_ic_particles(PState<R> s, const R* __restrict__ p1x, const R* 
 }
 
 template <typename R>
-__global__ void k_paint(PState<R> s, R* __restrict__ rho, int M, R mass, long long np) {
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) k_paint(PState<R> s, R* __restrict__ rho, int M, R mass, long long np) {
+  __shared__ R wsm[256];
+  R* ws = wsm + (threadIdx.x & ~31);
+  // whole warps iterate together (warp-aggregated atomics); lanes past the end add 0
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); j0 < np; j0 += stride) {
+    const long long j = j0 + (threadIdx.x & 31);
+    const bool valid = j < np;
+    const long long jj = valid ? j : np - 1;
     int ix, iy, iz;
-    unpack(s.cell[j], ix, iy, iz);
-    scatter(rho, corners(M, ix, iy, iz), s.fx[j], s.fy[j], s.fz[j], mass);
+    unpack(s.cell[jj], ix, iy, iz);
+    scatter_agg(rho, corners(M, ix, iy, iz), s.fx[jj], s.fy[jj], s.fz[jj], mass, valid, ws);
   }
 }
 
 // kick with the force at the current positions, drift, paint the new position
 template <typename R>
-__global__ void k_kdk_paint(PState<R> s, const R* __restrict__ F0, const R* __restrict__ F1,
-                            const R* __restrict__ F2, R* __restrict__ rho, int M, R ckick, R cdrift, R mass,
-                            long long np) {
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+__global__ void __launch_bounds__(256) k_kdk_paint(PState<R> s, const R* __restrict__ F0, const R* __restrict__ F1,
+                                                   const R* __restrict__ F2, R* __restrict__ rho, int M, R ckick,
+                                                   R cdrift, R mass, long long np) {
+  __shared__ R wsm[256];
+  R* ws = wsm + (threadIdx.x & ~31);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); j0 < np; j0 += stride) {
+    const long long j = j0 + (threadIdx.x & 31);
+    const bool valid = j < np;
+    const long long jj = valid ? j : np - 1;
     int ix, iy, iz;
-    unpack(s.cell[j], ix, iy, iz);
-    R fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
+    unpack(s.cell[jj], ix, iy, iz);
+    R fx = s.fx[jj], fy = s.fy[jj], fz = s.fz[jj];
     const Corners c = corners(M, ix, iy, iz);
-    const R px = s.px[j] + ckick * gather(F0, c, fx, fy, fz);
-    const R py = s.py[j] + ckick * gather(F1, c, fx, fy, fz);
-    const R pz = s.pz[j] + ckick * gather(F2, c, fx, fy, fz);
-    s.px[j] = px; s.py[j] = py; s.pz[j] = pz;
+    const R px = s.px[jj] + ckick * gather(F0, c, fx, fy, fz);
+    const R py = s.py[jj] + ckick * gather(F1, c, fx, fy, fz);
+    const R pz = s.pz[jj] + ckick * gather(F2, c, fx, fy, fz);
     // drift in cell units; carry the integer part into the cell index
     R nx = fx + px * cdrift, ny = fy + py * cdrift, nz = fz + pz * cdrift;
     R cx = floor(nx), cy = floor(ny), cz = floor(nz);
@@ -193,23 +223,29 @@ __global__ void k_kdk_paint(PState<R> s, const R* __restrict__ F0, const R* __re
     ix = wrap32(ix + (int)cx, M);
     iy = wrap32(iy + (int)cy, M);
     iz = wrap32(iz + (int)cz, M);
-    s.cell[j] = pack(ix, iy, iz);
-    s.fx[j] = nx; s.fy[j] = ny; s.fz[j] = nz;
-    scatter(rho, corners(M, ix, iy, iz), nx, ny, nz, mass);
+    if (valid) {
+      s.px[j] = px; s.py[j] = py; s.pz[j] = pz;
+      s.cell[j] = pack(ix, iy, iz);
+      s.fx[j] = nx; s.fy[j] = ny; s.fz[j] = nz;
+    }
+    scatter_agg(rho, corners(M, ix, iy, iz), nx, ny, nz, mass, valid, ws);
   }
 }
 
+// readout at the particles, written in lattice order (out[pid[j]])
 template <typename R>
-__global__ void k_readout(PState<R> s, const R* __restrict__ m0, const R* __restrict__ m1,
-                          const R* __restrict__ m2, int M, double scale, double* __restrict__ out, long long np) {
+__global__ void k_readout(PState<R> s, const uint32_t* __restrict__ pid, const R* __restrict__ m0,
+                          const R* __restrict__ m1, const R* __restrict__ m2, int M, double scale,
+                          double* __restrict__ out, long long np) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
     int ix, iy, iz;
     unpack(s.cell[j], ix, iy, iz);
     const Corners c = corners(M, ix, iy, iz);
     const R fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
-    out[3 * j + 0] = scale * (double)gather(m0, c, fx, fy, fz);
-    out[3 * j + 1] = scale * (double)gather(m1, c, fx, fy, fz);
-    out[3 * j + 2] = scale * (double)gather(m2, c, fx, fy, fz);
+    const long long o = pid[j];
+    out[3 * o + 0] = scale * (double)gather(m0, c, fx, fy, fz);
+    out[3 * o + 1] = scale * (double)gather(m1, c, fx, fy, fz);
+    out[3 * o + 2] = scale * (double)gather(m2, c, fx, fy, fz);
   }
 }
 
@@ -231,20 +267,21 @@ __global__ void k_set_particles(PState<R> s, const double* __restrict__ x, const
 }
 
 template <typename R>
-__global__ void k_get_particles(PState<R> s, double* __restrict__ x, double* __restrict__ p, double len_per_cell,
-                                long long np) {
+__global__ void k_get_particles(PState<R> s, const uint32_t* __restrict__ pid, double* __restrict__ x,
+                                double* __restrict__ p, double len_per_cell, long long np) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
     int ix, iy, iz;
     unpack(s.cell[j], ix, iy, iz);
+    const long long o = pid[j];  // lattice order
     if (x) {
-      x[3 * j + 0] = ((double)ix + (double)s.fx[j]) * len_per_cell;
-      x[3 * j + 1] = ((double)iy + (double)s.fy[j]) * len_per_cell;
-      x[3 * j + 2] = ((double)iz + (double)s.fz[j]) * len_per_cell;
+      x[3 * o + 0] = ((double)ix + (double)s.fx[j]) * len_per_cell;
+      x[3 * o + 1] = ((double)iy + (double)s.fy[j]) * len_per_cell;
+      x[3 * o + 2] = ((double)iz + (double)s.fz[j]) * len_per_cell;
     }
     if (p) {
-      p[3 * j + 0] = (double)s.px[j] * len_per_cell;
-      p[3 * j + 1] = (double)s.py[j] * len_per_cell;
-      p[3 * j + 2] = (double)s.pz[j] * len_per_cell;
+      p[3 * o + 0] = (double)s.px[j] * len_per_cell;
+      p[3 * o + 1] = (double)s.py[j] * len_per_cell;
+      p[3 * o + 2] = (double)s.pz[j] * len_per_cell;
     }
   }
 }
@@ -309,8 +346,9 @@ cudaError_t launch_kdk_paint(pm_ctx* c, R* rho, double ckick, double cdrift) {
 template <typename R>
 cudaError_t launch_readout(pm_ctx* c, R* const* meshes, double scale, double* out) {
   ProfScope ps(&c->prof, KK_MISC, c->stream);
-  k_readout<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), meshes[0], meshes[1], meshes[2], c->M,
-                                                             scale, out, c->np);
+  k_readout<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(
+      pstate<R>(c), reinterpret_cast<const uint32_t*>(c->ws + c->L.pid), meshes[0], meshes[1], meshes[2], c->M, scale,
+      out, c->np);
   return cudaGetLastError();
 }
 
@@ -325,7 +363,8 @@ cudaError_t launch_set_particles(pm_ctx* c, const double* x, const double* p) {
 template <typename R>
 cudaError_t launch_get_particles(pm_ctx* c, double* x, double* p) {
   ProfScope ps(&c->prof, KK_MISC, c->stream);
-  k_get_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), x, p, c->cfg.box / c->M, c->np);
+  k_get_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(
+      pstate<R>(c), reinterpret_cast<const uint32_t*>(c->ws + c->L.pid), x, p, c->cfg.box / c->M, c->np);
   return cudaGetLastError();
 }
 

@@ -95,6 +95,7 @@ enum TabId { T_D1 = 0, T_INVA, T_DD1, T_DINVA, T_D1P, T_D1M, T_INVAP, T_INVAM, T
 // workspace layout (byte offsets)
 struct Layout {
   size_t cell, frac, mom, fmesh, smesh, maps, flags, sqrtp, tab_d1, tab_inva;
+  size_t pid, cell2, frac2, mom2, pid2, sort_cnt;  // original index, sort double buffer, bucket counts
   size_t scratch;  // start of the scratch union
   // step scratch
   size_t rho, cbuf, ubuf;
@@ -197,6 +198,17 @@ template <typename R>
 cudaError_t launch_convert_in(const double* in, R* out, long long n, cudaStream_t s, Prof* pf);
 template <typename R>
 cudaError_t launch_convert_out(const R* in, double* out, long long n, double scale, cudaStream_t s, Prof* pf);
+
+// spatial sort (sort.cu)
+void launch_iota(pm_ctx* c);
+template <typename R>
+cudaError_t sort_particles(pm_ctx* c);
+template <typename R>
+cudaError_t launch_unpermute3(pm_ctx* c, const R* src, const uint32_t* pid, R* dst);
+template <typename R>
+cudaError_t launch_permute3(pm_ctx* c, const R* src, const uint32_t* pid, R* dst);
+size_t sort_scratch_bytes(int M);
+inline int sort_every(const pm_config& cfg) { return cfg.ckpt_every > 0 ? cfg.ckpt_every : 4; }
 
 // lensing (lens.cu)
 template <typename R>

