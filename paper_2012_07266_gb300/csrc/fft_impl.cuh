@@ -278,6 +278,42 @@ __device__ __forceinline__ void store_tile(typename CT<R>::T* dst, const typenam
   }
 }
 
+// store i k * tile: k = k_x of each column (per_column) or the scalar `kc`
+template <typename R, int N, int W, int THREADS>
+__device__ __forceinline__ void store_tile_ik(typename CT<R>::T* dst, const typename CT<R>::T* src, long long rstride,
+                                              int nv, int kx0, R kf, R kc, bool per_column) {
+  using C = typename CT<R>::T;
+  constexpr int h = N / 2;
+  auto kof = [&](int c) -> R {
+    const int ix = kx0 + c;
+    return per_column ? (ix == h ? R(0) : kf * (R)(ix <= h ? ix : ix - N)) : kc;
+  };
+  if constexpr (sizeof(R) == 4 && W % 2 == 0) {
+    constexpr int WP = W / 2, PER = N * WP / THREADS;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      const int row = e / WP, c = 2 * (e - row * WP);
+      const float4 v = reinterpret_cast<const float4*>(src)[e];
+      const R k0 = kof(c), k1 = kof(c + 1);
+      const float4 o = make_float4(-k0 * v.y, k0 * v.x, -k1 * v.w, k1 * v.z);
+      C* g = dst + row * rstride + c;
+      if (c + 1 < nv) *reinterpret_cast<float4*>(g) = o;
+      else if (c < nv) g[0] = C{o.x, o.y};
+    }
+  } else {
+    constexpr int PER = N * W / THREADS;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * THREADS;
+      const int row = e / W, c = e - row * W;
+      const R k = kof(c);
+      const C b = src[e];
+      if (c < nv) dst[row * rstride + c] = C{-k * b.y, k * b.x};
+    }
+  }
+}
+
 // ---------------------------------------------------------------- kernels
 // x pass, forward: real rows -> half-spectrum rows
 template <typename R, int N>
@@ -456,6 +492,20 @@ __device__ __forceinline__ void spec_coef(const SpecParams& sp, int o, int ix, i
   }
 }
 
+// g(k) of the force (3/2 Om scale / k^2) or PGD (alpha O_L O_S scale / k^2) operators,
+// whose j-th output multiplies by i k_j g(k)
+template <typename R>
+__device__ __forceinline__ R force_g(const SpecParams& sp, bool pgd, int ix, int iy, int iz, int n) {
+  const int h = n / 2;
+  const int fx = ix <= h ? ix : ix - n, fy = iy <= h ? iy : iy - n, fz = iz <= h ? iz : iz - n;
+  const R kf = (R)sp.kf;
+  const R k2 = kf * kf * (R)(fx * fx + fy * fy + fz * fz);
+  if (!(k2 > R(0))) return R(0);
+  const R inv = R(1) / k2;
+  if (!pgd) return (R)sp.scale * inv;
+  return (R)sp.pgd_scale * inv * exp(-(R)(sp.kl * sp.kl) * inv) * exp(-pow(sqrt(k2) / (R)sp.ks, (R)sp.nexp));
+}
+
 template <typename R>
 __device__ __forceinline__ typename CT<R>::T spec_mult(const SpecParams& sp, int o, int ix, int iy, int iz,
                                                        int n, typename CT<R>::T a) {
@@ -507,31 +557,56 @@ k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int
         gp[q] = (R)sp.pgd_scale * inv * exp(-(R)(sp.kl * sp.kl) * inv) * exp(-pow(sqrt(k2) / (R)sp.ks, (R)sp.nexp));
     }
   }
-  for (int o = 0; o < nout; ++o) {
-    if (force) {
-      const R kf = (R)sp.kf;
-      const int h = N / 2;
-      const int ax = o % 3;
+  if (force) {
+    // i k_x and i k_y are constant along a z column: F_x = i k_x IFFT_z(g A) and
+    // F_y = i k_y IFFT_z(g A) share one inverse transform; F_z = IFFT_z(i k_z g A)
+    // needs its own (likewise for the PGD outputs with gp).
+    const R kf = (R)sp.kf;
+    const int h = N / 2;
+    const R oy = iy == h ? R(0) : kf * (R)(iy <= h ? iy : iy - N);
+    const int npass = nout == 6 ? 4 : 2;
+    for (int pass = 0; pass < npass; ++pass) {
+      const bool zc = pass & 1;  // the z component's own transform
+      const bool pg = pass >= 2;
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
         const int e = threadIdx.x + q * THR;
-        const int row = e / W, c = e - row * W;
-        const int idx = ax == 0 ? kx0 + c : (ax == 1 ? iy : row);
-        const R odd = idx == h ? R(0) : kf * (R)(idx <= h ? idx : idx - N);
-        const R s = (o < 3 ? g[q] : gp[q]) * odd;  // multiplier i * s
+        const int row = e / W;
+        const R gg = pg ? gp[q] : g[q];
         const C a = A[e];
-        B[e] = C{-s * a.y, s * a.x};
+        if (zc) {
+          const R oz = row == h ? R(0) : kf * (R)(row <= h ? row : row - N);
+          const R s = gg * oz;  // multiplier i * s
+          B[e] = C{-s * a.y, s * a.x};
+        } else {
+          B[e] = C{gg * a.x, gg * a.y};
+        }
       }
-    } else {
+      __syncthreads();
+      fft_column<C, N, true, W, 1>(B, col, t, tw);
+      const int o0 = pg ? 3 : 0;
+      if (zc) {
+        store_tile<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o0 + 2]) + plane, B, rstride, nv);
+      } else {
+        // two outputs from one transform: i k_x (per column) and i k_y (per block) times it
+        store_tile_ik<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o0]) + plane, B, rstride, nv,
+                                                      kx0, kf, R(0), true);
+        store_tile_ik<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o0 + 1]) + plane, B, rstride, nv,
+                                                      kx0, kf, oy, false);
+      }
+      __syncthreads();
+    }
+  } else {
+    for (int o = 0; o < nout; ++o) {
       for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
         const int row = e / W, c = e - row * W;
         B[e] = spec_mult<R>(sp, o, kx0 + c, iy, row, N, A[e]);
       }
+      __syncthreads();
+      fft_column<C, N, true, W, 1>(B, col, t, tw);
+      store_tile<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o]) + plane, B, rstride, nv);
+      __syncthreads();
     }
-    __syncthreads();
-    fft_column<C, N, true, W, 1>(B, col, t, tw);
-    store_tile<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o]) + plane, B, rstride, nv);
-    __syncthreads();
   }
 }
 
@@ -556,7 +631,57 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
   const int nv = min(W, ncols - kx0);
   const int col = threadIdx.x % W, t = threadIdx.x / W;
   for (int e = threadIdx.x; e < N * W; e += blockDim.x) B[e] = C{0, 0};
-  for (int c = 0; c < nin; ++c) {
+  const bool force3 = (sp.op == OP_FORCE || sp.op == OP_FORCE_PGD) && nin == 3 && (first == 0 || first == 3);
+  if (force3) {
+    // conj(i k_x g) FFT(A_x) + conj(i k_y g) FFT(A_y) = -i g FFT(k_x A_x + k_y A_y):
+    // k_x, k_y are constant along the column, so one forward transform serves both
+    constexpr int THR = ZTile<R, N>::THREADS;
+    constexpr int EPT = N * W / THR;
+    const R kf = (R)sp.kf;
+    const int h = N / 2;
+    const R oy = iy == h ? R(0) : kf * (R)(iy <= h ? iy : iy - N);
+    load_tile<R, N, W, THR>(A, reinterpret_cast<const C*>(ins.p[0]) + plane, rstride, nv);
+    __syncthreads();
+    {
+      const C* iny = reinterpret_cast<const C*>(ins.p[1]) + plane;
+      C vy[EPT];
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = threadIdx.x + q * THR;
+        const int row = e / W, cc = e - row * W;
+        vy[q] = cc < nv ? iny[row * rstride + cc] : C{0, 0};
+      }
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = threadIdx.x + q * THR;
+        const int ix = kx0 + (e - (e / W) * W);
+        const R ox = ix == h ? R(0) : kf * (R)(ix <= h ? ix : ix - N);
+        const C a = A[e];
+        A[e] = C{ox * a.x + oy * vy[q].x, ox * a.y + oy * vy[q].y};
+      }
+    }
+    __syncthreads();
+    fft_column<C, N, false, W, 1>(A, col, t, tw);
+    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+      const int row = e / W, cc = e - row * W;
+      const R g = force_g<R>(sp, first >= 3, kx0 + cc, iy, row, N);
+      const C a = A[e];
+      B[e] = C{g * a.y, -g * a.x};  // -i g a
+    }
+    __syncthreads();
+    load_tile<R, N, W, THR>(A, reinterpret_cast<const C*>(ins.p[2]) + plane, rstride, nv);
+    __syncthreads();
+    fft_column<C, N, false, W, 1>(A, col, t, tw);
+    for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
+      const int row = e / W, cc = e - row * W;
+      R re, im;
+      spec_coef<R>(sp, first + 2, kx0 + cc, iy, row, N, re, im);
+      const C a = A[e];
+      B[e] = C{B[e].x + im * a.y, B[e].y - im * a.x};  // + conj(i im) a
+    }
+    __syncthreads();
+  }
+  for (int c = 0; c < (force3 ? 0 : nin); ++c) {
     const C* in = reinterpret_cast<const C*>(ins.p[c]);
     load_tile<R, N, W, ZTile<R, N>::THREADS>(A, in + plane, rstride, nv);
     __syncthreads();
