@@ -139,14 +139,16 @@ void build_tables(pm_ctx* c) {
   c->chi_tab_h = c->chi_tab_max / (kChiTab - 1);
   // mean-density term: (3/2) Om (H0/c)^2 int_0^chi_s chi (chi_s - chi) / (chi_s a) dchi (Simpson)
   for (int s = 0; s < PM_MAX_ZS; ++s) c->mean_term[s] = 0.0;
+  std::vector<double> ag(8001);
   for (int s = 0; s < cfg.n_zs; ++s) {
     const double cs = c->chi_s[s];
     const int m = 8000;
     const double hh = cs / m;
+    co.a_of_chi_grid(hh, m + 1, ag.data());
     double acc = 0;
     for (int k = 0; k <= m; ++k) {
       const double x = k * hh;
-      const double f = x * (cs - x) / (cs * co.a_of_chi(x));
+      const double f = x * (cs - x) / (cs * ag[k]);
       acc += (k == 0 || k == m ? 1.0 : (k & 1 ? 4.0 : 2.0)) * f;
     }
     c->mean_term[s] = 1.5 * cfg.omega_m / (kCoverH0 * kCoverH0) * acc * hh / 3.0;
@@ -184,14 +186,16 @@ void build_adjoint_tables(pm_ctx* c) {
     }
     cs.resize(cfg.n_zs);
     for (int s = 0; s < PM_MAX_ZS; ++s) mt[s] = 0.0;
+    std::vector<double> ag(8001);
     for (int s = 0; s < cfg.n_zs; ++s) {
       cs[s] = co.chi_a(1.0 / (1.0 + cfg.zs[s]));
       const int m = 8000;
       const double hh = cs[s] / m;
+      co.a_of_chi_grid(hh, m + 1, ag.data());
       double acc = 0;
       for (int q = 0; q <= m; ++q) {
         const double x = q * hh;
-        acc += (q == 0 || q == m ? 1.0 : (q & 1 ? 4.0 : 2.0)) * x * (cs[s] - x) / (cs[s] * co.a_of_chi(x));
+        acc += (q == 0 || q == m ? 1.0 : (q & 1 ? 4.0 : 2.0)) * x * (cs[s] - x) / (cs[s] * ag[q]);
       }
       mt[s] = 1.5 * om / (kCoverH0 * kCoverH0) * acc * hh / 3.0;
     }
@@ -201,12 +205,15 @@ void build_adjoint_tables(pm_ctx* c) {
 cudaError_t upload_adjoint_tables(pm_ctx* c) {
   const pm_config& cfg = c->cfg;
   std::vector<double> dd1(kChiTab), dinva(kChiTab), d1p(kChiTab), d1m(kChiTab), ivp(kChiTab), ivm(kChiTab);
+  std::vector<double> ag(kChiTab), agp(kChiTab), agm(kChiTab);
+  c->cosmo.a_of_chi_grid(c->chi_tab_h, kChiTab, ag.data());
+  c->cos_p.a_of_chi_grid(c->chi_tab_h, kChiTab, agp.data());
+  c->cos_m.a_of_chi_grid(c->chi_tab_h, kChiTab, agm.data());
   for (int k = 0; k < kChiTab; ++k) {
-    const double x = k * c->chi_tab_h;
-    const double a = c->cosmo.a_of_chi(x);
+    const double a = ag[k];
     dd1[k] = -c->cosmo.gp(a) / (a * kCoverH0);  // dD1(a(chi))/dchi
     dinva[k] = c->cosmo.E(a) / kCoverH0;        // d(1/a)/dchi
-    const double ap = c->cos_p.a_of_chi(x), am = c->cos_m.a_of_chi(x);
+    const double ap = agp[k], am = agm[k];
     d1p[k] = c->cos_p.D1(ap);
     d1m[k] = c->cos_m.D1(am);
     ivp[k] = 1.0 / ap;
@@ -240,9 +247,10 @@ cudaError_t upload_adjoint_tables(pm_ctx* c) {
 
 cudaError_t upload_tables(pm_ctx* c) {
   const pm_config& cfg = c->cfg;
-  std::vector<double> d1t(kChiTab), inva(kChiTab);
+  std::vector<double> d1t(kChiTab), inva(kChiTab), ag(kChiTab);
+  c->cosmo.a_of_chi_grid(c->chi_tab_h, kChiTab, ag.data());
   for (int k = 0; k < kChiTab; ++k) {
-    const double a = c->cosmo.a_of_chi(k * c->chi_tab_h);
+    const double a = ag[k];
     d1t[k] = c->cosmo.D1(a);
     inva[k] = 1.0 / a;
   }

@@ -36,6 +36,7 @@ struct Cosmo {
   double gf(double a) const;   // a^2 E dgp/da
   double chi_a(double a) const;
   double a_of_chi(double c) const;
+  void a_of_chi_grid(double h, int n, double* out) const;  // a(q h), q < n, O(n) sweep
   double transfer(double k_hmpc) const;  // Eisenstein & Hu (1998) with BAO
   double pk(double k_hmpc) const;        // sigma8-normalised linear P(k), z = 0
 };
