@@ -12,7 +12,9 @@ struct Launch {
   // algorithmic bytes of one pass: real mesh R, unpadded half-spectrum C
   static constexpr double RB = (double)N * N * N * sizeof(R);
   static constexpr double CB = (double)N * N * (N / 2 + 1) * sizeof(C);
-  static size_t smem_x() { return (size_t)(N / 2 + RowTile<R, N>::ROWS * (PadLen<N / 2>::value + 1)) * sizeof(C); }
+  static size_t smem_x() {
+    return (size_t)(N / 2 + N / 2 + 2 + RowTile<R, N>::ROWS * (PadLen<N / 2>::value + 1)) * sizeof(C);
+  }
   static size_t smem_cols() { return (size_t)(N + N * ColTile<R, N>::W) * sizeof(C); }
   static size_t smem_z() { return (size_t)(N + 2 * N * ZTile<R, N>::W) * sizeof(C); }
   static int ntiles() { return (N / 2 + 1 + ColTile<R, N>::W - 1) / ColTile<R, N>::W; }

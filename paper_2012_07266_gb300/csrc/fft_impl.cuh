@@ -121,23 +121,36 @@ template <> struct Plan<1024> { static constexpr int V = 8; using Rad = Radices<
 __device__ __forceinline__ int pad16(int k) { return k + (k >> 4); }
 template <int H> struct PadLen { static constexpr int value = H + H / 16; };
 
-// One Stockham stage over a column of N elements at buf[row * rs + col * cs]
-// (RS == 1: buf[pad16(row) + col * cs]); T = N / V threads per column, thread
-// t handles V / RAD butterflies.
-template <typename C, int N, int V, int RAD, bool INV, int NS, int RS, int CS>
+// One Stockham stage over CP adjacent columns of N elements at
+// buf[row * RS + col * CS] (RS == 1: buf[pad16(row) + col * CS]); T = N / V
+// threads per column group, thread t handles V / RAD butterflies of each of
+// its CP columns with one set of twiddles.  Two adjacent FP32 columns
+// (CS == 1) move as one 16-byte shared-memory access.
+template <typename C, int N, int V, int RAD, bool INV, int NS, int RS, int CS, int CP>
 __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
-  constexpr int cs = CS;
-  auto at = [&](int row) -> C& { return RS == 1 ? buf[pad16(row) + col * cs] : buf[row * RS + col * cs]; };
+  constexpr bool VEC = CP == 2 && CS == 1 && RS != 1 && sizeof(C) == 8;
+  auto at = [&](int row, int cc) -> C& {
+    return RS == 1 ? buf[pad16(row) + (col + cc) * CS] : buf[row * RS + (col + cc) * CS];
+  };
   constexpr int T = N / V;
   constexpr int NB = V / RAD;
   constexpr int NR = N / RAD;
   constexpr int TSTR = N / (NS * RAD);
-  C v[NB][RAD];
+  C v[CP][NB][RAD];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int j = t + b * T;
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) v[b][k] = at(j + k * NR);
+    for (int k = 0; k < RAD; ++k) {
+      if constexpr (VEC) {
+        const float4 q = *reinterpret_cast<const float4*>(&at(j + k * NR, 0));
+        v[0][b][k] = C{q.x, q.y};
+        v[CP - 1][b][k] = C{q.z, q.w};
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < CP; ++cc) v[cc][b][k] = at(j + k * NR, cc);
+      }
+    }
   }
   __syncthreads();
 #pragma unroll
@@ -149,33 +162,44 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
       for (int k = 1; k < RAD; ++k) {
         C w = tw[jm * k * TSTR];
         if (INV) w.y = -w.y;
-        v[b][k] = cmul(v[b][k], w);
+#pragma unroll
+        for (int cc = 0; cc < CP; ++cc) v[cc][b][k] = cmul(v[cc][b][k], w);
       }
     }
-    dft<RAD, INV>(v[b]);
+#pragma unroll
+    for (int cc = 0; cc < CP; ++cc) dft<RAD, INV>(v[cc][b]);
     const int base = (j - jm) * RAD + jm;
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) at(base + k * NS) = v[b][k];
+    for (int k = 0; k < RAD; ++k) {
+      if constexpr (VEC) {
+        *reinterpret_cast<float4*>(&at(base + k * NS, 0)) =
+            make_float4(v[0][b][k].x, v[0][b][k].y, v[CP - 1][b][k].x, v[CP - 1][b][k].y);
+      } else {
+#pragma unroll
+        for (int cc = 0; cc < CP; ++cc) at(base + k * NS, cc) = v[cc][b][k];
+      }
+    }
   }
   __syncthreads();
 }
 
-template <typename C, int N, int V, bool INV, int RS, int CS, int NS, int RAD, int... Rest>
+template <typename C, int N, int V, bool INV, int RS, int CS, int CP, int NS, int RAD, int... Rest>
 __device__ __forceinline__ void run_stages(C* buf, int col, int t, const C* tw) {
-  stage<C, N, V, RAD, INV, NS, RS, CS>(buf, col, t, tw);
-  if constexpr (sizeof...(Rest) > 0) run_stages<C, N, V, INV, RS, CS, NS * RAD, Rest...>(buf, col, t, tw);
+  stage<C, N, V, RAD, INV, NS, RS, CS, CP>(buf, col, t, tw);
+  if constexpr (sizeof...(Rest) > 0) run_stages<C, N, V, INV, RS, CS, CP, NS * RAD, Rest...>(buf, col, t, tw);
 }
 
-template <typename C, int N, bool INV, int RS, int CS, int... Rs>
+template <typename C, int N, bool INV, int RS, int CS, int CP, int... Rs>
 __device__ __forceinline__ void fft_column_impl(Radices<Rs...>, C* buf, int col, int t, const C* tw) {
-  run_stages<C, N, Plan<N>::V, INV, RS, CS, 1, Rs...>(buf, col, t, tw);
+  run_stages<C, N, Plan<N>::V, INV, RS, CS, CP, 1, Rs...>(buf, col, t, tw);
 }
 
-// In-place FFT of one column of length N held in shared memory: element k of
-// column `col` at buf[k * RS + col * CS] (compile-time strides).
-template <typename C, int N, bool INV, int RS, int CS>
+// In-place FFT of CP adjacent columns of length N held in shared memory:
+// element k of column `col + c` at buf[k * RS + (col + c) * CS] (compile-time
+// strides).
+template <typename C, int N, bool INV, int RS, int CS, int CP = 1>
 __device__ __forceinline__ void fft_column(C* buf, int col, int t, const C* tw) {
-  fft_column_impl<C, N, INV, RS, CS>(typename Plan<N>::Rad{}, buf, col, t, tw);
+  fft_column_impl<C, N, INV, RS, CS, CP>(typename Plan<N>::Rad{}, buf, col, t, tw);
 }
 
 // tw[m] = exp(-2 pi i m / N), m < N
@@ -189,20 +213,39 @@ template <typename C, int N> __device__ __forceinline__ void make_twiddles(C* tw
   }
 }
 
+// tu[k] = exp(-2 pi i k / N), k <= N / 2 (real <-> half-length complex untangling)
+template <typename C, int N> __device__ __forceinline__ void make_untangle(C* tu) {
+  using R = decltype(C{}.x);
+  for (int m = threadIdx.x; m <= N / 2; m += blockDim.x) {
+    R s, c;
+    if constexpr (sizeof(R) == 4) sincospif(-2.0f * (float)m / (float)N, &s, &c);
+    else sincospi(-2.0 * (double)m / (double)N, &s, &c);
+    tu[m] = C{c, s};
+  }
+}
+
 // ------------------------------------------------------------ tile widths
+// CP: columns per thread (two adjacent FP32 columns share twiddles, index
+// arithmetic and 16-byte shared-memory accesses)
 template <typename R, int N> struct ColTile {
   static constexpr int cap_smem = (sizeof(R) == 4 ? 8192 : 4096) / N;  // N*W*sizeof(C) <= 64 KB
   static constexpr int cap_thr = 1024 * Plan<N>::V / N;
   static constexpr int cap = cap_smem < cap_thr ? (cap_smem < 32 ? cap_smem : 32) : (cap_thr < 32 ? cap_thr : 32);
   static constexpr int W = cap >= 32 ? 32 : cap >= 16 ? 16 : cap >= 8 ? 8 : cap >= 4 ? 4 : cap >= 2 ? 2 : 1;
-  static constexpr int THREADS = W * (N / Plan<N>::V);
+  static constexpr int CP = (sizeof(R) == 4 && W >= 2) ? 2 : 1;
+  static constexpr int THREADS = W / CP * (N / Plan<N>::V);
 };
 
 // fused z pass: half the column tile of the plain passes for large N, so that
-// two blocks (two A/B buffer pairs) share an SM and overlap load and compute
+// several blocks (A/B buffer pairs) share an SM and overlap load and compute
 template <typename R, int N> struct ZTile {
-  static constexpr int W = (N >= 256 && ColTile<R, N>::W >= 2) ? ColTile<R, N>::W / 2 : ColTile<R, N>::W;
-  static constexpr int THREADS = W * (N / Plan<N>::V);
+  static constexpr int W = (N >= 256 && ColTile<R, N>::W >= 4) ? ColTile<R, N>::W / 2 : ColTile<R, N>::W;
+  static constexpr int CP = (sizeof(R) == 4 && W >= 2) ? 2 : 1;
+  static constexpr int THREADS = W / CP * (N / Plan<N>::V);
+  static constexpr int SMEM = (N + 2 * N * W) * (int)sizeof(R) * 2;
+  // two resident blocks: the operator passes need ~128 registers per thread
+  // (a third block's register cap spills, measured slower)
+  static constexpr int MINB = (227 * 1024 / SMEM) >= 2 ? 2 : 1;
 };
 
 template <typename R, int N> struct RowTile {  // x pass: rows of N reals, FFT length N/2
@@ -323,8 +366,10 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   constexpr int H = N / 2, ROWS = RowTile<R, N>::ROWS, T = RowTile<R, N>::T, LD = PadLen<H>::value + 1;
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* buf = tw + H;
+  C* tu = tw + H;        // untangle twiddles exp(-2 pi i k / N), k <= H
+  C* buf = tu + H + 2;
   make_twiddles<C, H>(tw);
+  make_untangle<C, N>(tu);
   const long long row0 = (long long)blockIdx.x * ROWS;
   {
     // ROWS consecutive rows are contiguous: ROWS * H complex values, read as pairs
@@ -358,17 +403,19 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
   fft_column<C, H, false, 1, LD>(buf, h, t, tw);
-  for (int e = threadIdx.x; e < ROWS * (H + 1); e += blockDim.x) {
-    const int hh = e / (H + 1), k = e - hh * (H + 1);
+  // X[k] = (Z[k] + conj Z[H-k]) / 2 + e^{-2 pi i k / N} (Z[k] - conj Z[H-k]) / (2i), k <= H
+  auto untangle = [&](int hh, int k) {
     const C zk = buf[hh * LD + pad16(k % H)];
     const C zm = cconj(buf[hh * LD + pad16((H - k) % H)]);
     const C ev = C{R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y)};
     const C od = C{R(0.5) * (zk.y - zm.y), -R(0.5) * (zk.x - zm.x)};  // (zk - zm) / (2i)
-    R s, c;
-    if constexpr (sizeof(R) == 4) sincospif(-2.0f * (float)k / (float)N, &s, &c);
-    else sincospi(-2.0 * (double)k / (double)N, &s, &c);
-    out[(row0 + hh) * P + k] = cadd(ev, cmul(C{c, s}, od));
+    out[(row0 + hh) * P + k] = cadd(ev, cmul(tu[k], od));
+  };
+  for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
+    const int hh = e / H;
+    untangle(hh, e - hh * H);
   }
+  for (int hh = threadIdx.x; hh < ROWS; hh += blockDim.x) untangle(hh, H);
 }
 
 // x pass, inverse: half-spectrum rows -> real rows (unnormalised: n * IDFT)
@@ -379,7 +426,7 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
   constexpr int H = N / 2, ROWS = RowTile<R, N>::ROWS, T = RowTile<R, N>::T, LD = PadLen<H>::value + 1;
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
-  C* buf = tw + H;
+  C* buf = tw + H + H + 2;
   make_twiddles<C, H>(tw);
   const long long row0 = (long long)blockIdx.x * ROWS;
   constexpr int THR = RowTile<R, N>::THREADS, PER = ROWS * H / THR;
@@ -416,7 +463,7 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
 
 // y or z pass in place: column tiles of W kx values over a full axis.
 template <typename R, int N, bool INV>
-__global__ void __launch_bounds__(ColTile<R, N>::THREADS, 2048 / ColTile<R, N>::THREADS)
+__global__ void __launch_bounds__(ColTile<R, N>::THREADS, (1024 / ColTile<R, N>::THREADS) > 0 ? 1024 / ColTile<R, N>::THREADS : 1)
 k_fft_cols(typename CT<R>::T* __restrict__ data, long long plane_stride, long long row_stride, int ncols) {
   using C = typename CT<R>::T;
   constexpr int W = ColTile<R, N>::W;
@@ -429,12 +476,27 @@ k_fft_cols(typename CT<R>::T* __restrict__ data, long long plane_stride, long lo
   const int nv = min(W, ncols - kx0);
   load_tile<R, N, W, ColTile<R, N>::THREADS>(buf, base, row_stride, nv);
   __syncthreads();
-  const int col = threadIdx.x % W, t = threadIdx.x / W;
-  fft_column<C, N, INV, W, 1>(buf, col, t, tw);
+  constexpr int CP = ColTile<R, N>::CP;
+  const int col = CP * (threadIdx.x % (W / CP)), t = threadIdx.x / (W / CP);
+  fft_column<C, N, INV, W, 1, CP>(buf, col, t, tw);
   store_tile<R, N, W, ColTile<R, N>::THREADS>(base, buf, row_stride, nv);
 }
 
 struct OutPtrs { void* p[9]; };
+
+// PGD filter O_L O_S = exp(-(k_l/k)^2) exp(-(k/k_s)^n) (Eq. 12-13) at k^2 > 0, inv = 1/k^2.
+// FP32 evaluates it in log space with the hardware exp/log approximations
+// ((k/k_s)^n = exp(n (ln k^2 / 2 - ln k_s)); relative error ~1e-6, far below
+// the FP32 path's tolerance); FP64 uses the libm functions.
+template <typename R>
+__device__ __forceinline__ R pgd_filter(const SpecParams& sp, R k2, R inv) {
+  if constexpr (sizeof(R) == 4) {
+    const float kl2 = (float)(sp.kl * sp.kl), nexp = (float)sp.nexp, lks = __logf((float)sp.ks);
+    return __expf(-kl2 * inv - __expf(nexp * (0.5f * __logf(k2) - lks)));
+  } else {
+    return exp(-(sp.kl * sp.kl) * inv) * exp(-pow(sqrt(k2) / sp.ks, sp.nexp));
+  }
+}
 
 // Fourier-space operator of output o at integer frequencies: multiplier re + i im.
 template <typename R>
@@ -454,11 +516,7 @@ __device__ __forceinline__ void spec_coef(const SpecParams& sp, int o, int ix, i
     case OP_FORCE_PGD: {
       const R odd = o % 3 == 0 ? ox : (o % 3 == 1 ? oy : oz);
       R s = (R)sp.scale;
-      if (o >= 3) {
-        const R kk = sqrt(k2);
-        const R filt = k2 > R(0) ? exp(-(R)(sp.kl * sp.kl) * inv) * exp(-pow(kk / (R)sp.ks, (R)sp.nexp)) : R(0);
-        s = (R)sp.pgd_scale * filt;
-      }
+      if (o >= 3) s = k2 > R(0) ? (R)sp.pgd_scale * pgd_filter<R>(sp, k2, inv) : R(0);
       im = s * odd * inv;
       break;
     }
@@ -503,7 +561,7 @@ __device__ __forceinline__ R force_g(const SpecParams& sp, bool pgd, int ix, int
   if (!(k2 > R(0))) return R(0);
   const R inv = R(1) / k2;
   if (!pgd) return (R)sp.scale * inv;
-  return (R)sp.pgd_scale * inv * exp(-(R)(sp.kl * sp.kl) * inv) * exp(-pow(sqrt(k2) / (R)sp.ks, (R)sp.nexp));
+  return (R)sp.pgd_scale * inv * pgd_filter<R>(sp, k2, inv);
 }
 
 template <typename R>
@@ -517,10 +575,10 @@ __device__ __forceinline__ typename CT<R>::T spec_mult(const SpecParams& sp, int
 
 // fused z pass: forward z FFT, per-output multiplier, inverse z FFT, store.
 template <typename R, int N>
-__global__ void __launch_bounds__(ZTile<R, N>::THREADS)
+__global__ void __launch_bounds__(ZTile<R, N>::THREADS, ZTile<R, N>::MINB)
 k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int P, SpecParams sp) {
   using C = typename CT<R>::T;
-  constexpr int W = ZTile<R, N>::W;
+  constexpr int W = ZTile<R, N>::W, CP = ZTile<R, N>::CP;
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* A = tw + N;
@@ -534,65 +592,54 @@ k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int
   const int nv = min(W, ncols - kx0);
   load_tile<R, N, W, ZTile<R, N>::THREADS>(A, in + plane, rstride, nv);
   __syncthreads();
-  const int col = threadIdx.x % W, t = threadIdx.x / W;
-  fft_column<C, N, false, W, 1>(A, col, t, tw);
+  const int col = CP * (threadIdx.x % (W / CP)), t = threadIdx.x / (W / CP);
+  fft_column<C, N, false, W, 1, CP>(A, col, t, tw);
   constexpr int THR = ZTile<R, N>::THREADS;
-  constexpr int EPT = N * W / THR;  // elements per thread, fixed across outputs
+  constexpr int EPT = N * W / THR;  // elements per thread, the same set in every loop below
   const bool force = sp.op == OP_FORCE || sp.op == OP_FORCE_PGD;
-  R g[EPT], gp[EPT];
-  if (force) {
-    // (3/2) Om / k^2 and alpha O_L O_S / k^2 per element, once for all outputs
-    const R kf = (R)sp.kf;
-    const int h = N / 2;
-#pragma unroll
-    for (int q = 0; q < EPT; ++q) {
-      const int e = threadIdx.x + q * THR;
-      const int row = e / W, c = e - row * W, ix = kx0 + c;
-      const int fx = ix <= h ? ix : ix - N, fy = iy <= h ? iy : iy - N, fz = row <= h ? row : row - N;
-      const R k2 = kf * kf * (R)(fx * fx + fy * fy + fz * fz);
-      const R inv = k2 > R(0) ? R(1) / k2 : R(0);
-      g[q] = (R)sp.scale * inv;
-      gp[q] = R(0);
-      if (sp.op == OP_FORCE_PGD && k2 > R(0))
-        gp[q] = (R)sp.pgd_scale * inv * exp(-(R)(sp.kl * sp.kl) * inv) * exp(-pow(sqrt(k2) / (R)sp.ks, (R)sp.nexp));
-    }
-  }
   if (force) {
     // i k_x and i k_y are constant along a z column: F_x = i k_x IFFT_z(g A) and
     // F_y = i k_y IFFT_z(g A) share one inverse transform; F_z = IFFT_z(i k_z g A)
-    // needs its own (likewise for the PGD outputs with gp).
+    // needs its own.  A is scaled in place, first by g = (3/2) Om / k^2, then
+    // (PGD outputs) by gp / g = (alpha / (3/2 Om)) O_L O_S, so that no
+    // per-element factor is kept in registers; the last transform runs on A.
     const R kf = (R)sp.kf;
     const int h = N / 2;
     const R oy = iy == h ? R(0) : kf * (R)(iy <= h ? iy : iy - N);
+    const int fy = iy <= h ? iy : iy - N;
     const int npass = nout == 6 ? 4 : 2;
+    const R pratio = (R)(sp.pgd_scale / sp.scale);
     for (int pass = 0; pass < npass; ++pass) {
-      const bool zc = pass & 1;  // the z component's own transform
-      const bool pg = pass >= 2;
+      const bool zc = pass & 1;  // the z component's transform
+      const bool last = pass == npass - 1;
+      C* T = last ? A : B;
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
         const int e = threadIdx.x + q * THR;
-        const int row = e / W;
-        const R gg = pg ? gp[q] : g[q];
-        const C a = A[e];
-        if (zc) {
-          const R oz = row == h ? R(0) : kf * (R)(row <= h ? row : row - N);
-          const R s = gg * oz;  // multiplier i * s
-          B[e] = C{-s * a.y, s * a.x};
+        const int row = e / W, c = e - row * W, ix = kx0 + c;
+        C a = A[e];
+        if (!zc) {
+          const int fx = ix <= h ? ix : ix - N, fz = row <= h ? row : row - N;
+          const R k2 = kf * kf * (R)(fx * fx + fy * fy + fz * fz);
+          const R inv = k2 > R(0) ? R(1) / k2 : R(0);
+          const R f = pass == 0 ? (R)sp.scale * inv : (k2 > R(0) ? pratio * pgd_filter<R>(sp, k2, inv) : R(0));
+          a = C{f * a.x, f * a.y};
+          A[e] = a;
+          T[e] = a;
         } else {
-          B[e] = C{gg * a.x, gg * a.y};
+          const R oz = row == h ? R(0) : kf * (R)(row <= h ? row : row - N);
+          T[e] = C{-oz * a.y, oz * a.x};  // i k_z a
         }
       }
       __syncthreads();
-      fft_column<C, N, true, W, 1>(B, col, t, tw);
-      const int o0 = pg ? 3 : 0;
+      fft_column<C, N, true, W, 1, CP>(T, col, t, tw);
+      const int o0 = pass >= 2 ? 3 : 0;
       if (zc) {
-        store_tile<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o0 + 2]) + plane, B, rstride, nv);
+        store_tile<R, N, W, THR>(reinterpret_cast<C*>(outs.p[o0 + 2]) + plane, T, rstride, nv);
       } else {
         // two outputs from one transform: i k_x (per column) and i k_y (per block) times it
-        store_tile_ik<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o0]) + plane, B, rstride, nv,
-                                                      kx0, kf, R(0), true);
-        store_tile_ik<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o0 + 1]) + plane, B, rstride, nv,
-                                                      kx0, kf, oy, false);
+        store_tile_ik<R, N, W, THR>(reinterpret_cast<C*>(outs.p[o0]) + plane, T, rstride, nv, kx0, kf, R(0), true);
+        store_tile_ik<R, N, W, THR>(reinterpret_cast<C*>(outs.p[o0 + 1]) + plane, T, rstride, nv, kx0, kf, oy, false);
       }
       __syncthreads();
     }
@@ -603,8 +650,8 @@ k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int
         B[e] = spec_mult<R>(sp, o, kx0 + c, iy, row, N, A[e]);
       }
       __syncthreads();
-      fft_column<C, N, true, W, 1>(B, col, t, tw);
-      store_tile<R, N, W, ZTile<R, N>::THREADS>(reinterpret_cast<C*>(outs.p[o]) + plane, B, rstride, nv);
+      fft_column<C, N, true, W, 1, CP>(B, col, t, tw);
+      store_tile<R, N, W, THR>(reinterpret_cast<C*>(outs.p[o]) + plane, B, rstride, nv);
       __syncthreads();
     }
   }
@@ -614,7 +661,7 @@ struct InPtrs { const void* p[9]; };
 
 // transposed fused z pass: B = sum_c conj(m_{first+c}(k)) FFT_z(A_c); store IFFT_z(B)
 template <typename R, int N>
-__global__ void __launch_bounds__(ZTile<R, N>::THREADS)
+__global__ void __launch_bounds__(ZTile<R, N>::THREADS, ZTile<R, N>::MINB)
 k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ out, int P, SpecParams sp) {
   using C = typename CT<R>::T;
   constexpr int W = ZTile<R, N>::W;
@@ -629,7 +676,8 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
   const long long plane = (long long)iy * P + kx0;
   const long long rstride = (long long)N * P;
   const int nv = min(W, ncols - kx0);
-  const int col = threadIdx.x % W, t = threadIdx.x / W;
+  constexpr int CP = ZTile<R, N>::CP;
+  const int col = CP * (threadIdx.x % (W / CP)), t = threadIdx.x / (W / CP);
   for (int e = threadIdx.x; e < N * W; e += blockDim.x) B[e] = C{0, 0};
   const bool force3 = (sp.op == OP_FORCE || sp.op == OP_FORCE_PGD) && nin == 3 && (first == 0 || first == 3);
   if (force3) {
@@ -661,7 +709,7 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
       }
     }
     __syncthreads();
-    fft_column<C, N, false, W, 1>(A, col, t, tw);
+    fft_column<C, N, false, W, 1, CP>(A, col, t, tw);
     for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
       const int row = e / W, cc = e - row * W;
       const R g = force_g<R>(sp, first >= 3, kx0 + cc, iy, row, N);
@@ -671,7 +719,7 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
     __syncthreads();
     load_tile<R, N, W, THR>(A, reinterpret_cast<const C*>(ins.p[2]) + plane, rstride, nv);
     __syncthreads();
-    fft_column<C, N, false, W, 1>(A, col, t, tw);
+    fft_column<C, N, false, W, 1, CP>(A, col, t, tw);
     for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
       const int row = e / W, cc = e - row * W;
       R re, im;
@@ -685,7 +733,7 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
     const C* in = reinterpret_cast<const C*>(ins.p[c]);
     load_tile<R, N, W, ZTile<R, N>::THREADS>(A, in + plane, rstride, nv);
     __syncthreads();
-    fft_column<C, N, false, W, 1>(A, col, t, tw);
+    fft_column<C, N, false, W, 1, CP>(A, col, t, tw);
     for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
       const int row = e / W, cc = e - row * W;
       R re, im;
@@ -696,7 +744,7 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
     }
     __syncthreads();
   }
-  fft_column<C, N, true, W, 1>(B, col, t, tw);
+  fft_column<C, N, true, W, 1, CP>(B, col, t, tw);
   store_tile<R, N, W, ZTile<R, N>::THREADS>(out + plane, B, rstride, nv);
 }
 
