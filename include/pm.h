@@ -21,7 +21,9 @@
  *    enqueued; a failing check returns PM_ERR_ARG / PM_ERR_STATE /
  *    PM_ERR_WORKSPACE / PM_ERR_UNSUPPORTED and enqueues nothing.  A CUDA
  *    launch error returns PM_ERR_CUDA.  Non-finite values met on the device
- *    set a flag that the synchronising calls report as PM_ERR_NONFINITE.
+ *    set a flag that the synchronising calls report as PM_ERR_NONFINITE; a
+ *    bounded device-side wait for a bulk copy that gave up sets another
+ *    flag, reported as PM_ERR_TIMEOUT.
  *  - Layouts: particle arrays are row-major (N, 3) with N = nc^3 and particle
  *    j = (jz * nc + jy) * nc + jx; meshes are [z][y][x] with x fastest;
  *    maps are [source][iy][ix] with ix along theta_x.
@@ -46,7 +48,10 @@ typedef enum {
   PM_ERR_CUDA = 3,        /* a CUDA call or launch failed                 */
   PM_ERR_NONFINITE = 4,   /* NaN/Inf met on the device                    */
   PM_ERR_STATE = 5,       /* entry point called out of order              */
-  PM_ERR_UNSUPPORTED = 6  /* size not supported by the FFT plans          */
+  PM_ERR_UNSUPPORTED = 6, /* size not supported by the FFT plans          */
+  PM_ERR_TIMEOUT = 7      /* a device-side wait for an asynchronous copy
+                             ran out of its iteration bound (the kernel
+                             returned early; results are invalid)         */
 } pm_status;
 
 enum { PM_FP32 = 0, PM_FP64 = 1 };

@@ -29,6 +29,7 @@ UNITS = [
     ("capi.cu", "capi.o", []),
     ("cosmo.cpp", "cosmo.o", []),
     ("prof.cpp", "prof.o", []),
+    ("tma_map.cpp", "tma_map.o", []),
     ("static_forces.cu", "static_forces.o", []),
     ("adjoint.cu", "adjoint.o", []),
     ("sort.cu", "sort.o", []),

@@ -276,8 +276,8 @@ cudaError_t upload_tables(pm_ctx* c) {
 template <typename R>
 cudaError_t force_from_rho(pm_ctx* c, bool with_pgd, double alpha_pgd) {
   const pm_config& cfg = c->cfg;
-  SpecParams sp;
-  std::memset(&sp, 0, sizeof(sp));
+  SpecParams sp = {};
+  sp.err = timeout_ptr(c);
   sp.op = with_pgd ? OP_FORCE_PGD : OP_FORCE;
   sp.kf = 2.0 * M_PI / cfg.box;
   const double m3 = (double)c->M * c->M * c->M;
@@ -321,8 +321,8 @@ pm_status do_ic(pm_ctx* c, const double* d_noise) {
   R* outs[13];
   for (int o = 0; o < 9; ++o) ub[o] = c->ws + c->L.ic_u + o * al(cgrid_bytes(c));
   for (int o = 0; o < 13; ++o) outs[o] = rp<R>(c, c->L.ic_out + o * al(g * c->rsz));
-  SpecParams sp;
-  std::memset(&sp, 0, sizeof(sp));
+  SpecParams sp = {};
+  sp.err = timeout_ptr(c);
   sp.op = cfg.lpt_order == 2 ? OP_LPT2_DERIV : OP_LPT1;
   sp.kf = 2.0 * M_PI / cfg.box;
   sp.scale = 1.0 / (double)g;
@@ -515,8 +515,8 @@ cudaError_t force_at_working(pm_ctx* c, bool pgd, double alpha) {
 }
 
 SpecParams force_params(pm_ctx* c, bool pgd, double alpha) {
-  SpecParams sp;
-  std::memset(&sp, 0, sizeof(sp));
+  SpecParams sp = {};
+  sp.err = timeout_ptr(c);
   const double m3 = (double)c->M * c->M * c->M;
   sp.op = pgd ? OP_FORCE_PGD : OP_FORCE;
   sp.kf = 2.0 * M_PI / c->cfg.box;
@@ -698,8 +698,8 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
   void* ub[9];
   for (int o = 0; o < 9; ++o) ub[o] = c->ws + c->L.ic_u + o * al(cgrid_bytes(c));
   auto lpt_forward = [&](const double* sqrtp) -> cudaError_t {
-    SpecParams sp;
-    std::memset(&sp, 0, sizeof(sp));
+    SpecParams sp = {};
+    sp.err = timeout_ptr(c);
     sp.op = two ? OP_LPT2_DERIV : OP_LPT1;
     sp.kf = 2.0 * M_PI / cfg.box;
     sp.scale = 1.0 / (double)g;
@@ -735,8 +735,8 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
   R* lpsi2[3] = {field(16), field(17), field(18)};
   adj_combine2<R>(lx, lp, lpsi1, co.D1(a0), co.gp(a0), cpl, g, s, pf);
   for (int q = 0; q < 3; ++q) adj_dot<R>(lpsi1[q], field(q), g, acc_ic + 2, s, pf);
-  SpecParams sp;
-  std::memset(&sp, 0, sizeof(sp));
+  SpecParams sp = {};
+  sp.err = timeout_ptr(c);
   sp.kf = 2.0 * M_PI / cfg.box;
   sp.scale = 1.0 / (double)g;
   sp.sqrtp = reinterpret_cast<const double*>(c->ws + c->L.sqrtp);
@@ -786,10 +786,10 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
 }
 
 pm_status read_flags(pm_ctx* c) {
-  int h = 0;
-  if (cudaMemcpyAsync(&h, c->ws + c->L.flags, sizeof(int), cudaMemcpyDeviceToHost, c->stream)) return PM_ERR_CUDA;
+  int h[2] = {0, 0};  // non-finite word, timeout word
+  if (cudaMemcpyAsync(h, c->ws + c->L.flags, sizeof(h), cudaMemcpyDeviceToHost, c->stream)) return PM_ERR_CUDA;
   if (cudaStreamSynchronize(c->stream)) return PM_ERR_CUDA;
-  return h ? PM_ERR_NONFINITE : PM_OK;
+  return h[1] ? PM_ERR_TIMEOUT : (h[0] ? PM_ERR_NONFINITE : PM_OK);
 }
 
 #define PM_DISPATCH(c, FN, ...) ((c)->prec == PM_FP64 ? FN<double>(__VA_ARGS__) : FN<float>(__VA_ARGS__))
@@ -818,7 +818,7 @@ template <typename R>
 pm_status do_fft(pm_ctx* c, const double* in, double* out) {
   R* rho = rp<R>(c, c->L.rho);
   if (launch_convert_in<R>(in, rho, c->mesh_elems, c->stream, &c->prof)) return PM_ERR_CUDA;
-  if (fft3d_r2c<R>(rho, c->ws + c->L.cbuf, c->M, c->P, c->stream, &c->prof)) return PM_ERR_CUDA;
+  if (fft3d_r2c<R>(rho, c->ws + c->L.cbuf, c->M, c->P, c->stream, &c->prof, timeout_ptr(c))) return PM_ERR_CUDA;
   using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
   ProfScope ps(&c->prof, KK_MISC, c->stream);
   k_unpad_complex<R><<<1024, 256, 0, c->stream>>>(reinterpret_cast<const C*>(c->ws + c->L.cbuf), out, c->M, c->P);
@@ -979,6 +979,7 @@ const char* pm_strerror(pm_status s) {
     case PM_ERR_NONFINITE: return "non-finite value on the device";
     case PM_ERR_STATE: return "entry point called out of order";
     case PM_ERR_UNSUPPORTED: return "unsupported size or feature";
+    case PM_ERR_TIMEOUT: return "device-side wait for a bulk copy timed out";
     default: return "unknown status";
   }
 }

@@ -1,6 +1,9 @@
 // Launchers of the 3D FFT passes and of the fused spectral operators.
+#include <algorithm>
+
 #include "adjoint.h"
 #include "fft_impl.cuh"
+#include "fft_tma.cuh"
 
 namespace pmlens {
 
@@ -18,6 +21,19 @@ struct Launch {
   static size_t smem_cols() { return (size_t)(N + N * ColTile<R, N>::W) * sizeof(C); }
   static size_t smem_z() { return (size_t)(N + 2 * N * ZTile<R, N>::W) * sizeof(C); }
   static int ntiles() { return (N / 2 + 1 + ColTile<R, N>::W - 1) / ColTile<R, N>::W; }
+  using TT = TmaTile<R, N>;
+  // persistent TMA column passes: one block per SM slot the occupancy allows
+  static int tma_grid(int tiles) {
+    static const int slots = [] {
+      int per_sm = 0, dev = 0, nsm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_cols_tma<R, N, false, false>, TT::THREADS,
+                                                    TT::SMEM);
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      return std::max(per_sm, 1) * std::max(nsm, 1);
+    }();
+    return std::min(tiles, slots);
+  }
 
   static void attrs() {
     static bool done = false;
@@ -28,6 +44,10 @@ struct Launch {
     cudaFuncSetAttribute(k_fft_cols<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols());
     cudaFuncSetAttribute(k_zpass_op<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z());
     cudaFuncSetAttribute(k_zpass_combine<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z());
+    cudaFuncSetAttribute(k_fft_cols_tma<R, N, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
+    cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
+    cudaFuncSetAttribute(k_fft_cols_tma<R, N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
+    cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
     done = true;
   }
 
@@ -39,19 +59,34 @@ struct Launch {
     ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_X_INV, s, RB + CB);
     k_fft_x_c2r<R, N><<<(long long)N * N / RowTile<R, N>::ROWS, RowTile<R, N>::THREADS, smem_x(), s>>>(in, out, P);
   }
+  // column pass over all N planes through the TMA pipeline (err != null) or
+  // the plain tile kernel
+  template <bool ZAXIS>
+  static cudaError_t cols_tma(C* d, int P, bool inv, cudaStream_t s, int* err) {
+    CUtensorMap map;
+    if (!make_cols_map(&map, d, N, P, TT::W, TT::BOXR, ZAXIS, sizeof(R) == 8)) return cudaErrorInvalidValue;
+    const int ntx = (N / 2 + 1 + TT::W - 1) / TT::W, tiles = ntx * N;
+    if (inv) k_fft_cols_tma<R, N, true, ZAXIS><<<tma_grid(tiles), TT::THREADS, TT::SMEM, s>>>(map, ntx, tiles, err);
+    else k_fft_cols_tma<R, N, false, ZAXIS><<<tma_grid(tiles), TT::THREADS, TT::SMEM, s>>>(map, ntx, tiles, err);
+    return cudaSuccess;
+  }
   // y pass: planes = z (stride N*P), rows = y (stride P)
-  static void y(C* d, int P, bool inv, cudaStream_t s, Prof* pf, int kind) {
+  static cudaError_t y(C* d, int P, bool inv, cudaStream_t s, Prof* pf, int kind, int* err) {
     ProfScope ps(pf, kind >= 0 ? kind : (inv ? KK_FFT_Y_INV : KK_FFT_Y_FWD), s, 2 * CB);
+    if (err) return cols_tma<false>(d, P, inv, s, err);
     dim3 g(ntiles(), N);
     if (inv) k_fft_cols<R, N, true><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, (long long)N * P, P, N / 2 + 1);
     else k_fft_cols<R, N, false><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, (long long)N * P, P, N / 2 + 1);
+    return cudaSuccess;
   }
   // z pass: planes = y (stride P), rows = z (stride N*P)
-  static void z(C* d, int P, bool inv, cudaStream_t s, Prof* pf, int kind) {
+  static cudaError_t z(C* d, int P, bool inv, cudaStream_t s, Prof* pf, int kind, int* err) {
     ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_Z_FWD, s, 2 * CB);
+    if (err) return cols_tma<true>(d, P, inv, s, err);
     dim3 g(ntiles(), N);
     if (inv) k_fft_cols<R, N, true><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, P, (long long)N * P, N / 2 + 1);
     else k_fft_cols<R, N, false><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, P, (long long)N * P, N / 2 + 1);
+    return cudaSuccess;
   }
   static void zop(const C* in, const OutPtrs& o, int nout, int P, const SpecParams& sp, cudaStream_t s,
                   Prof* pf, int kind) {
@@ -65,29 +100,31 @@ struct Launch {
     attrs();
     InPtrs ip;
     for (int i = 0; i < 9; ++i) ip.p[i] = i < nin ? ubufs[i] : nullptr;
-    for (int i = 0; i < nin; ++i) {
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nin && !e; ++i) {
       C* u = reinterpret_cast<C*>(ubufs[i]);
       x_fwd(real_in[i], u, P, s, pf, KK_ADJ);
-      y(u, P, false, s, pf, KK_ADJ);
+      e = y(u, P, false, s, pf, KK_ADJ, sp.err);
     }
+    if (e) return e;
     C* c = reinterpret_cast<C*>(cbuf);
     {
       ProfScope ps(pf, KK_ADJ, s, (nin + 1) * CB);
       dim3 g((N / 2 + 1 + ZTile<R, N>::W - 1) / ZTile<R, N>::W, N);
       k_zpass_combine<R, N><<<g, ZTile<R, N>::THREADS, smem_z(), s>>>(ip, nin, first, c, P, sp);
     }
-    y(c, P, true, s, pf, KK_ADJ);
+    if ((e = y(c, P, true, s, pf, KK_ADJ, sp.err))) return e;
     x_inv(c, real_out, P, s, pf, KK_ADJ);
     return cudaGetLastError();
   }
 
-  static cudaError_t r2c(const R* real, void* cplx, int P, cudaStream_t s, Prof* pf) {
+  static cudaError_t r2c(const R* real, void* cplx, int P, cudaStream_t s, Prof* pf, int* err) {
     attrs();
     C* c = reinterpret_cast<C*>(cplx);
     x_fwd(real, c, P, s, pf, -1);
-    y(c, P, false, s, pf, -1);
-    z(c, P, false, s, pf, -1);
-    return cudaGetLastError();
+    cudaError_t e = y(c, P, false, s, pf, -1, err);
+    if (!e) e = z(c, P, false, s, pf, -1, err);
+    return e ? e : cudaGetLastError();
   }
 
   static cudaError_t apply(const R* real_in, void* cbuf, void* const* ubufs, R* const* real_out, int nout, int P,
@@ -95,13 +132,14 @@ struct Launch {
     attrs();
     C* c = reinterpret_cast<C*>(cbuf);
     x_fwd(real_in, c, P, s, pf, kind);
-    y(c, P, false, s, pf, kind);
+    cudaError_t e = y(c, P, false, s, pf, kind, sp.err);
+    if (e) return e;
     OutPtrs o;
     for (int i = 0; i < 9; ++i) o.p[i] = i < nout ? ubufs[i] : nullptr;
     zop(c, o, nout, P, sp, s, pf, kind);
     for (int i = 0; i < nout; ++i) {
       C* u = reinterpret_cast<C*>(ubufs[i]);
-      y(u, P, true, s, pf, kind);
+      if ((e = y(u, P, true, s, pf, kind, sp.err))) return e;
       x_inv(u, real_out[i], P, s, pf, kind);
     }
     return cudaGetLastError();
@@ -124,8 +162,8 @@ struct Launch {
 }  // namespace
 
 template <typename R>
-cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s, Prof* pf) {
-  PM_FFT_DISPATCH(n, L::r2c(real, cplx, P, s, pf));
+cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s, Prof* pf, int* err) {
+  PM_FFT_DISPATCH(n, L::r2c(real, cplx, P, s, pf, err));
 }
 
 template <typename R>
@@ -144,7 +182,7 @@ cudaError_t spectral_transpose(R* const* real_in, int nin, int first, void* cons
 
 template cudaError_t spectral_transpose<PM_REAL>(PM_REAL* const*, int, int, void* const*, void*, PM_REAL*, int, int,
                                                   const SpecParams&, cudaStream_t, Prof*);
-template cudaError_t fft3d_r2c<PM_REAL>(const PM_REAL*, void*, int, int, cudaStream_t, Prof*);
+template cudaError_t fft3d_r2c<PM_REAL>(const PM_REAL*, void*, int, int, cudaStream_t, Prof*, int*);
 template cudaError_t spectral_apply<PM_REAL>(const PM_REAL*, void*, void* const*, PM_REAL* const*, int, int, int,
                                               const SpecParams&, cudaStream_t, Prof*, int);
 

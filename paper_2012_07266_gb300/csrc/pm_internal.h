@@ -158,8 +158,10 @@ inline bool fft_supported(int n) {
   }
 }
 // real [n][n][n] -> spectrum [n][n][P] (forward, sign -1, unnormalised)
+// err: timeout word of the TMA-pipelined column passes (null: plain passes
+// without device-side waits)
 template <typename R>
-cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s, Prof* prof);
+cudaError_t fft3d_r2c(const R* real, void* cplx, int n, int P, cudaStream_t s, Prof* prof, int* err);
 // spectral operators applied in the fused z pass: out_o = mult_o(k) * spectrum
 enum SpecOp { OP_FORCE = 0, OP_FORCE_PGD = 1, OP_LPT1 = 2, OP_LPT2_DERIV = 3, OP_GRAD_NEG = 4,
               OP_IDENTITY = 5 };
@@ -170,6 +172,7 @@ struct SpecParams {
   double pgd_scale; // alpha * (M/L) / n^3
   double kl, ks, nexp;
   const double* sqrtp;  // table indexed by integer |n|^2 (OP_LPT*)
+  int* err;             // timeout word of the TMA column passes (null: plain passes)
 };
 // forward x,y passes of `real`, fused z pass (forward, multiply, inverse) into
 // nout complex buffers, then inverse y,x passes into the real outputs.
@@ -240,5 +243,6 @@ inline const R* chi_table(pm_ctx* c, int id) {
   }
 }
 inline int* flags_ptr(pm_ctx* c) { return reinterpret_cast<int*>(c->ws + c->L.flags); }
+inline int* timeout_ptr(pm_ctx* c) { return flags_ptr(c) + 1; }
 
 }  // namespace pmlens

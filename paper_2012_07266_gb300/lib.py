@@ -15,7 +15,7 @@ PM_FP32, PM_FP64 = 0, 1
 PM_MAX_ZS = 16
 
 STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_WORKSPACE", 3: "PM_ERR_CUDA",
-          4: "PM_ERR_NONFINITE", 5: "PM_ERR_STATE", 6: "PM_ERR_UNSUPPORTED"}
+          4: "PM_ERR_NONFINITE", 5: "PM_ERR_STATE", 6: "PM_ERR_UNSUPPORTED", 7: "PM_ERR_TIMEOUT"}
 
 # every symbol include/pm.h declares
 EXPORTS = ["pm_workspace_size", "pm_init", "pm_ic", "pm_step", "lens_project", "kappa_maps",
