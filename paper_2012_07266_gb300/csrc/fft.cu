@@ -48,6 +48,8 @@ struct Launch {
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
+    cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         TT::SMEM_DUAL);
     done = true;
   }
 
@@ -66,8 +68,31 @@ struct Launch {
     CUtensorMap map;
     if (!make_cols_map(&map, d, N, P, TT::W, TT::BOXR, ZAXIS, sizeof(R) == 8)) return cudaErrorInvalidValue;
     const int ntx = (N / 2 + 1 + TT::W - 1) / TT::W, tiles = ntx * N;
-    if (inv) k_fft_cols_tma<R, N, true, ZAXIS><<<tma_grid(tiles), TT::THREADS, TT::SMEM, s>>>(map, ntx, tiles, err);
-    else k_fft_cols_tma<R, N, false, ZAXIS><<<tma_grid(tiles), TT::THREADS, TT::SMEM, s>>>(map, ntx, tiles, err);
+    if (inv)
+      k_fft_cols_tma<R, N, true, ZAXIS><<<tma_grid(tiles), TT::THREADS, TT::SMEM, s>>>(map, map, ntx, tiles, err, R(0));
+    else
+      k_fft_cols_tma<R, N, false, ZAXIS><<<tma_grid(tiles), TT::THREADS, TT::SMEM, s>>>(map, map, ntx, tiles, err, R(0));
+    return cudaSuccess;
+  }
+  // inverse y pass of a shared x,y gradient spectrum G (in place): d <- i k_x IFFT_y(G),
+  // d2 <- IFFT_y(i k_y G)
+  static cudaError_t y_dual(C* d, C* d2, int P, double kf, cudaStream_t s, Prof* pf, int kind, int* err) {
+    ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_Y_INV, s, 3 * CB);
+    CUtensorMap map, map2;
+    if (!make_cols_map(&map, d, N, P, TT::W, TT::BOXR, false, sizeof(R) == 8) ||
+        !make_cols_map(&map2, d2, N, P, TT::W, TT::BOXR, false, sizeof(R) == 8))
+      return cudaErrorInvalidValue;
+    const int ntx = (N / 2 + 1 + TT::W - 1) / TT::W, tiles = ntx * N;
+    static const int slots = [] {
+      int per_sm = 0, dev = 0, nsm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_cols_tma<R, N, true, false, true>, TT::THREADS,
+                                                    TT::SMEM_DUAL);
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      return std::max(per_sm, 1) * std::max(nsm, 1);
+    }();
+    k_fft_cols_tma<R, N, true, false, true><<<std::min(tiles, slots), TT::THREADS, TT::SMEM_DUAL, s>>>(
+        map, map2, ntx, tiles, err, (R)kf);
     return cudaSuccess;
   }
   // y pass: planes = z (stride N*P), rows = y (stride P)
@@ -137,10 +162,22 @@ struct Launch {
     OutPtrs o;
     for (int i = 0; i < 9; ++i) o.p[i] = i < nout ? ubufs[i] : nullptr;
     zop(c, o, nout, P, sp, s, pf, kind);
-    for (int i = 0; i < nout; ++i) {
-      C* u = reinterpret_cast<C*>(ubufs[i]);
-      if ((e = y(u, P, true, s, pf, kind, sp.err))) return e;
-      x_inv(u, real_out[i], P, s, pf, kind);
+    const bool force = sp.op == OP_FORCE || sp.op == OP_FORCE_PGD;
+    if (force && sp.err && (nout == 3 || nout == 6)) {
+      // the z pass left G (x,y group) and the z component of each group of three
+      for (int g0 = 0; g0 < nout && !e; g0 += 3) {
+        e = y_dual(reinterpret_cast<C*>(ubufs[g0]), reinterpret_cast<C*>(ubufs[g0 + 1]), P, sp.kf, s, pf, kind,
+                   sp.err);
+        if (!e) e = y(reinterpret_cast<C*>(ubufs[g0 + 2]), P, true, s, pf, kind, sp.err);
+      }
+      for (int i = 0; i < nout && !e; ++i) x_inv(reinterpret_cast<C*>(ubufs[i]), real_out[i], P, s, pf, kind);
+      if (e) return e;
+    } else {
+      for (int i = 0; i < nout; ++i) {
+        C* u = reinterpret_cast<C*>(ubufs[i]);
+        if ((e = y(u, P, true, s, pf, kind, sp.err))) return e;
+        x_inv(u, real_out[i], P, s, pf, kind);
+      }
     }
     return cudaGetLastError();
   }

@@ -636,6 +636,9 @@ k_zpass_op(const typename CT<R>::T* __restrict__ in, OutPtrs outs, int nout, int
       const int o0 = pass >= 2 ? 3 : 0;
       if (zc) {
         store_tile<R, N, W, THR>(reinterpret_cast<C*>(outs.p[o0 + 2]) + plane, T, rstride, nv);
+      } else if (sp.err) {
+        // G itself: the dual inverse y pass applies i k_x and i k_y
+        store_tile<R, N, W, THR>(reinterpret_cast<C*>(outs.p[o0]) + plane, T, rstride, nv);
       } else {
         // two outputs from one transform: i k_x (per column) and i k_y (per block) times it
         store_tile_ik<R, N, W, THR>(reinterpret_cast<C*>(outs.p[o0]) + plane, T, rstride, nv, kx0, kf, R(0), true);

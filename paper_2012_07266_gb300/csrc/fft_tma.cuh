@@ -38,6 +38,7 @@ template <typename R, int N> struct TmaTile {
   static constexpr int TILE_BYTES = N * W * 2 * (int)sizeof(R);
   static constexpr int TW_BYTES = (N * 2 * (int)sizeof(R) + 1023) / 1024 * 1024;
   static constexpr int SMEM = TW_BYTES + 2 * TILE_BYTES + 64;  // + two mbarriers and a flag
+  static constexpr int SMEM_DUAL = TW_BYTES + 3 * TILE_BYTES + 64;  // + the second output's work tile
   static_assert(N % BOXR == 0, "box rows");
   static_assert((2 * W * (int)sizeof(R)) % 16 == 0, "TMA inner box extent must be a 16-byte multiple");
   static_assert(TILE_BYTES % 1024 == 0, "tile buffers stay 1024-byte aligned");
@@ -96,9 +97,15 @@ constexpr int PM_FLAG_TIMEOUT = 1;
 
 // ZAXIS: rows are z (box {2W, 1, BOXR}); else rows are y (box {2W, BOXR, 1}).
 // Tile ti: plane = ti / ntx (z for the y pass, y for the z pass), kx tile ti % ntx.
-template <typename R, int N, bool INV, bool ZAXIS>
+//
+// DUAL (inverse y pass of the force / PGD x,y components): the input tile
+// holds G = IFFT_z(g A); the block writes i k_x IFFT_y(G) in place and
+// IFFT_y(i k_y G) through map2 (k_x, k_y = kf times the signed frequency,
+// zero on the Nyquist plane), two transforms per tile read.
+template <typename R, int N, bool INV, bool ZAXIS, bool DUAL = false>
 __global__ void __launch_bounds__(TmaTile<R, N>::THREADS, TmaTile<R, N>::MINB)
-k_fft_cols_tma(const __grid_constant__ CUtensorMap map, int ntx, int ntiles, int* __restrict__ err) {
+k_fft_cols_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap map2, int ntx,
+               int ntiles, int* __restrict__ err, R kf) {
   using C = typename CT<R>::T;
   using TT = TmaTile<R, N>;
   constexpr int W = TT::W, CP = TT::CP;
@@ -106,7 +113,8 @@ k_fft_cols_tma(const __grid_constant__ CUtensorMap map, int ntx, int ntiles, int
   C* tw = reinterpret_cast<C*>(smem_tma);
   // tile buffer b at smem_tma + TW_BYTES + b * TILE_BYTES, its mbarrier at bar0 + 8 b
   auto buf = [&](int b) { return reinterpret_cast<C*>(smem_tma + TT::TW_BYTES + b * TT::TILE_BYTES); };
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tma + TT::TW_BYTES + 2 * TT::TILE_BYTES);
+  C* work2 = reinterpret_cast<C*>(smem_tma + TT::TW_BYTES + 2 * TT::TILE_BYTES);  // DUAL only
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_tma + TT::TW_BYTES + (DUAL ? 3 : 2) * TT::TILE_BYTES);
   int* ok_word = reinterpret_cast<int*>(bars + 2);
   const uint32_t bar0 = smem_u32(bars);
   auto bar = [&](int b) { return bar0 + 8u * (uint32_t)b; };
@@ -148,10 +156,11 @@ k_fft_cols_tma(const __grid_constant__ CUtensorMap map, int ntx, int ntiles, int
   for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
     const int b = it & 1;
     const int next = ti + gridDim.x;
-    if (leader && next < ntiles) {
-      // the other buffer's last bulk store must have read it before it is refilled
+    if (leader && (DUAL || next < ntiles)) {
+      // the other buffer's (and, DUAL, the second work tile's) last bulk store
+      // must have read shared memory before it is refilled
       bulk_wait_read0();
-      issue_load(next, b ^ 1);
+      if (next < ntiles) issue_load(next, b ^ 1);
     }
     // the leader polls (bounded) and broadcasts, so that all threads leave together
     if (leader) *ok_word = mbar_wait(bar(b), (it >> 1) & 1) ? 1 : 0;
@@ -165,6 +174,22 @@ k_fft_cols_tma(const __grid_constant__ CUtensorMap map, int ntx, int ntiles, int
       break;
     }
     mbar_wait(bar(b), (it >> 1) & 1);  // completed phase: returns at once, acquires the tile per thread
+    if constexpr (DUAL) {
+      // buf <- i k_x G, work2 <- i k_y G (rows are k_y, columns k_x)
+      constexpr int h = N / 2;
+      C* g = buf(b);
+      const int kx0 = (ti % ntx) * W;
+      for (int e = threadIdx.x; e < N * W; e += TT::THREADS) {
+        const int row = e / W, ix = kx0 + (e - row * W);
+        const R ox = ix == h ? R(0) : kf * (R)(ix <= h ? ix : ix - N);
+        const R oy = row == h ? R(0) : kf * (R)(row <= h ? row : row - N);
+        const C a = g[e];
+        g[e] = C{-ox * a.y, ox * a.x};
+        work2[e] = C{-oy * a.y, oy * a.x};
+      }
+      __syncthreads();
+      fft_column<C, N, INV, W, 1, CP>(work2, col, t, tw);
+    }
     fft_column<C, N, INV, W, 1, CP>(buf(b), col, t, tw);  // ends with __syncthreads
     fence_proxy_async();  // generic-proxy writes of the tile -> visible to the bulk store
     __syncthreads();
@@ -174,6 +199,7 @@ k_fft_cols_tma(const __grid_constant__ CUtensorMap map, int ntx, int ntiles, int
         int c0, c1, c2;
         coords(ti, q * TT::BOXR, c0, c1, c2);
         tma_store_3d(&map, c0, c1, c2, smem_u32(buf(b)) + q * TT::BOXR * W * (int)sizeof(C));
+        if constexpr (DUAL) tma_store_3d(&map2, c0, c1, c2, smem_u32(work2) + q * TT::BOXR * W * (int)sizeof(C));
       }
       bulk_commit();
     }
