@@ -23,6 +23,11 @@ namespace pmlens {
 
 namespace {
 
+template <typename T>
+__device__ __forceinline__ T pick3(int a, T v0, T v1, T v2) {
+  return a == 0 ? v0 : (a == 1 ? v1 : v2);
+}
+
 __device__ __forceinline__ void unpack3(uint32_t c, int* i) {
   i[0] = c & 1023u;
   i[1] = (c >> 10) & 1023u;
@@ -227,8 +232,8 @@ __global__ void __launch_bounds__(256) k_lens_vjp(const LensAdjArgs<R> A) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const int ax = rp.perm[d];
-        int i = ci[ax];
-        R f = cf[ax];
+        int i = pick3(ax, ci[0], ci[1], ci[2]);
+        R f = pick3(ax, cf[0], cf[1], cf[2]);
         if (rp.flip >> d & 1) {
           if (f > R(0)) { i = A.M - 1 - i; f = R(1) - f; }
           else { i = i == 0 ? 0 : A.M - i; }
@@ -260,8 +265,8 @@ __global__ void __launch_bounds__(256) k_lens_vjp(const LensAdjArgs<R> A) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         sg[d] = (rp.flip >> d & 1) ? R(-1) : R(1);
-        pr[d] = sg[d] * cp[rp.perm[d]];
-        sr[d] = sg[d] * cs[rp.perm[d]];
+        pr[d] = sg[d] * pick3((int)rp.perm[d], cp[0], cp[1], cp[2]);
+        sr[d] = sg[d] * pick3((int)rp.perm[d], cs[0], cs[1], cs[2]);
       }
       const R chi = sqrt(chi2);
       R rc[3] = {r[0], r[1], r[2]};
@@ -326,9 +331,16 @@ __global__ void __launch_bounds__(256) k_lens_vjp(const LensAdjArgs<R> A) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const int ax = rp.perm[d];
-        gx[ax] += sg[d] * gr[d] * cell_len;
-        if (A.sub) gp[ax] += sg[d] * grc[d] * dt * cell_len;
-        gs[ax] += sg[d] * grc[d] * cell_len;
+        const R vx = sg[d] * gr[d] * cell_len, vs = sg[d] * grc[d] * cell_len;
+        const R vp = A.sub ? vs * dt : R(0);
+        // scatter to the particle's own axis ax with constant indices (no local memory)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const bool hit = a == ax;
+          gx[a] += hit ? vx : R(0);
+          gp[a] += hit ? vp : R(0);
+          gs[a] += hit ? vs : R(0);
+        }
       }
     }
     A.lx[j] += gx[0];

@@ -59,6 +59,11 @@ __device__ __forceinline__ void block_sum(double v, double* acc) {
   }
 }
 
+template <typename T>
+__device__ __forceinline__ T pick3(int a, T v0, T v1, T v2) {
+  return a == 0 ? v0 : (a == 1 ? v1 : v2);
+}
+
 template <typename R>
 __device__ __forceinline__ R interp(const R* __restrict__ t, int n, R hinv, R x) {
   const R u = x * hinv;
@@ -92,10 +97,12 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.np;
        j += (long long)gridDim.x * blockDim.x) {
     const uint32_t c = A.cell[j];
-    const int ci[3] = {(int)(c & 1023u), (int)((c >> 10) & 1023u), (int)(c >> 20)};
-    const R cf[3] = {A.fx[j], A.fy[j], A.fz[j]};
-    const R cp[3] = {A.px[j], A.py[j], A.pz[j]};
-    R cs[3] = {R(0), R(0), R(0)};
+    // per-axis particle data in registers; a replica's axis permutation picks
+    // among them with selects (a runtime-indexed array would live in local memory)
+    const int ci0 = (int)(c & 1023u), ci1 = (int)((c >> 10) & 1023u), ci2 = (int)(c >> 20);
+    const R cf0 = A.fx[j], cf1 = A.fy[j], cf2 = A.fz[j];
+    const R cp0 = A.px[j], cp1 = A.py[j], cp2 = A.pz[j];
+    R cs0 = R(0), cs1 = R(0), cs2 = R(0);
     bool have_s = false;  // PGD displacement gathered only for particles that may land on the map
     for (int q = 0; q < A.nrep; ++q) {
       const Replica rp = A.rep[q];
@@ -103,8 +110,8 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const int ax = rp.perm[d];
-        int i = ci[ax];
-        R f = cf[ax];
+        int i = pick3(ax, ci0, ci1, ci2);
+        R f = pick3(ax, cf0, cf1, cf2);
         R sg = R(1);
         if (rp.flip >> d & 1) {
           if (f > R(0)) { i = A.M - 1 - i; f = R(1) - f; }
@@ -114,8 +121,8 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         i += rp.shift[d];
         if (i >= A.M) i -= A.M;
         r[d] = ((R)(i + rp.n[d] * A.M) + f) * cell_len;
-        pr[d] = sg * cp[ax];
-        sr[d] = sg * cs[ax];
+        pr[d] = sg * pick3(ax, cp0, cp1, cp2);
+        sr[d] = sg * pick3(ax, cs0, cs1, cs2);
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
       if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) continue;
@@ -123,12 +130,15 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
       const R lim = r[2] * tan_half + margin;
       if (fabs(r[0]) > lim || fabs(r[1]) > lim) continue;
       if (A.S0 && !have_s) {
-        cs[0] = gather3(A.S0, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
-        cs[1] = gather3(A.S1, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
-        cs[2] = gather3(A.S2, A.M, ci[0], ci[1], ci[2], cf[0], cf[1], cf[2]);
+        cs0 = gather3(A.S0, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
+        cs1 = gather3(A.S1, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
+        cs2 = gather3(A.S2, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
         have_s = true;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) sr[d] = (rp.flip >> d & 1) ? -cs[rp.perm[d]] : cs[rp.perm[d]];
+        for (int d = 0; d < 3; ++d) {
+          const R v = pick3((int)rp.perm[d], cs0, cs1, cs2);
+          sr[d] = (rp.flip >> d & 1) ? -v : v;
+        }
       }
       if (A.sub) {
         const R t = interp<R>(A.tab_d1, A.tab_n, (R)A.tab_hinv, sqrt(chi2));

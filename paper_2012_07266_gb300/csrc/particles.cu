@@ -9,7 +9,6 @@
 #include <cmath>
 
 #include "pm_internal.h"
-#include "warp_agg.cuh"
 
 namespace pmlens {
 
@@ -113,23 +112,6 @@ __device__ __forceinline__ void scatter(R* __restrict__ m, const Corners& c, R f
   atomicAdd(m + c.r11 + c.x1, w11 * fx);
 }
 
-// CIC scatter with warp-aggregated atomics; `valid` false adds nothing
-template <typename R>
-__device__ __forceinline__ void scatter_agg(R* __restrict__ m, const Corners& c, R fx, R fy, R fz, R w, bool valid,
-                                            R* wsm) {
-  const R gx = R(1) - fx, gy = R(1) - fy, gz = R(1) - fz;
-  const R wv = valid ? w : R(0);
-  const R w00 = wv * gz * gy, w01 = wv * gz * fy, w10 = wv * fz * gy, w11 = wv * fz * fy;
-  warp_agg_add(m, c.r00 + c.x0, w00 * gx, wsm);
-  warp_agg_add(m, c.r00 + c.x1, w00 * fx, wsm);
-  warp_agg_add(m, c.r01 + c.x0, w01 * gx, wsm);
-  warp_agg_add(m, c.r01 + c.x1, w01 * fx, wsm);
-  warp_agg_add(m, c.r10 + c.x0, w10 * gx, wsm);
-  warp_agg_add(m, c.r10 + c.x1, w10 * fx, wsm);
-  warp_agg_add(m, c.r11 + c.x0, w11 * gx, wsm);
-  warp_agg_add(m, c.r11 + c.x1, w11 * fx, wsm);
-}
-
 template <typename R>
 struct PState {
   uint32_t* cell;
@@ -178,19 +160,15 @@ __global__ void k_ic_particles(PState<R> s, const R* __restrict__ p1x, const R* 
   }
 }
 
+// CIC paint.  The state is kept sorted by coarse spatial bucket, so the
+// reductions of a warp hit few L2 lines; plain (vector) reductions measured
+// faster than warp-aggregating same-cell lanes first.
 template <typename R>
 __global__ void __launch_bounds__(256) k_paint(PState<R> s, R* __restrict__ rho, int M, R mass, long long np) {
-  __shared__ R wsm[256];
-  R* ws = wsm + (threadIdx.x & ~31);
-  // whole warps iterate together (warp-aggregated atomics); lanes past the end add 0
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long j0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); j0 < np; j0 += stride) {
-    const long long j = j0 + (threadIdx.x & 31);
-    const bool valid = j < np;
-    const long long jj = valid ? j : np - 1;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
     int ix, iy, iz;
-    unpack(s.cell[jj], ix, iy, iz);
-    scatter_agg(rho, corners(M, ix, iy, iz), s.fx[jj], s.fy[jj], s.fz[jj], mass, valid, ws);
+    unpack(s.cell[j], ix, iy, iz);
+    scatter(rho, corners(M, ix, iy, iz), s.fx[j], s.fy[j], s.fz[j], mass);
   }
 }
 
@@ -199,20 +177,14 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_kdk_paint(PState<R> s, const R* __restrict__ F0, const R* __restrict__ F1,
                                                    const R* __restrict__ F2, R* __restrict__ rho, int M, R ckick,
                                                    R cdrift, R mass, long long np) {
-  __shared__ R wsm[256];
-  R* ws = wsm + (threadIdx.x & ~31);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long j0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); j0 < np; j0 += stride) {
-    const long long j = j0 + (threadIdx.x & 31);
-    const bool valid = j < np;
-    const long long jj = valid ? j : np - 1;
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
     int ix, iy, iz;
-    unpack(s.cell[jj], ix, iy, iz);
-    R fx = s.fx[jj], fy = s.fy[jj], fz = s.fz[jj];
+    unpack(s.cell[j], ix, iy, iz);
+    R fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
     const Corners c = corners(M, ix, iy, iz);
-    const R px = s.px[jj] + ckick * gather(F0, c, fx, fy, fz);
-    const R py = s.py[jj] + ckick * gather(F1, c, fx, fy, fz);
-    const R pz = s.pz[jj] + ckick * gather(F2, c, fx, fy, fz);
+    const R px = s.px[j] + ckick * gather(F0, c, fx, fy, fz);
+    const R py = s.py[j] + ckick * gather(F1, c, fx, fy, fz);
+    const R pz = s.pz[j] + ckick * gather(F2, c, fx, fy, fz);
     // drift in cell units; carry the integer part into the cell index
     R nx = fx + px * cdrift, ny = fy + py * cdrift, nz = fz + pz * cdrift;
     R cx = floor(nx), cy = floor(ny), cz = floor(nz);
@@ -223,12 +195,10 @@ __global__ void __launch_bounds__(256) k_kdk_paint(PState<R> s, const R* __restr
     ix = wrap32(ix + (int)cx, M);
     iy = wrap32(iy + (int)cy, M);
     iz = wrap32(iz + (int)cz, M);
-    if (valid) {
-      s.px[j] = px; s.py[j] = py; s.pz[j] = pz;
-      s.cell[j] = pack(ix, iy, iz);
-      s.fx[j] = nx; s.fy[j] = ny; s.fz[j] = nz;
-    }
-    scatter_agg(rho, corners(M, ix, iy, iz), nx, ny, nz, mass, valid, ws);
+    s.px[j] = px; s.py[j] = py; s.pz[j] = pz;
+    s.cell[j] = pack(ix, iy, iz);
+    s.fx[j] = nx; s.fy[j] = ny; s.fz[j] = nz;
+    scatter(rho, corners(M, ix, iy, iz), nx, ny, nz, mass);
   }
 }
 
