@@ -126,6 +126,24 @@ template <int H> struct PadLen { static constexpr int value = H + H / 16; };
 // threads per column group, thread t handles V / RAD butterflies of each of
 // its CP columns with one set of twiddles.  Two adjacent FP32 columns
 // (CS == 1) move as one 16-byte shared-memory access.
+// Padded offset pad16(base + k * S) - pad16(base) when it is the same for every
+// base of the access pattern: (a) S a multiple of 16; (b) S | 16 and the base
+// is a multiple of 16 plus a remainder below S (block writes of a stage with
+// Ns * R a multiple of 16); (c) the R outputs of a butterfly sit inside one
+// aligned group of 16 (Ns * R | 16).  -1: no constant offset.
+template <int S, int R, bool WRITE, int NSR>
+__device__ __forceinline__ constexpr int pad_step(int k) {
+  if constexpr (S % 16 == 0) return k * S + k * S / 16;
+  else if constexpr (WRITE && 16 % S == 0 && NSR % 16 == 0) return k * S + (k * S) / 16;
+  else if constexpr (WRITE && 16 % NSR == 0) return k * S;
+  else return -1;
+}
+
+// One Stockham stage over CP adjacent columns of N elements at
+// buf[row * RS + col * CS] (RS == 1: buf[pad16(row) + col * CS]); T = N / V
+// threads per column group, thread t handles V / RAD butterflies of each of
+// its CP columns with one set of twiddles.  Two adjacent FP32 columns
+// (CS == 1) move as one 16-byte shared-memory access.
 template <typename C, int N, int V, int RAD, bool INV, int NS, int RS, int CS, int CP>
 __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
   constexpr bool VEC = CP == 2 && CS == 1 && RS != 1 && sizeof(C) == 8;
@@ -136,19 +154,28 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
   constexpr int NB = V / RAD;
   constexpr int NR = N / RAD;
   constexpr int TSTR = N / (NS * RAD);
+  // unit-stride (padded) columns: constant offsets from one padded base per butterfly
+  constexpr bool RD_CONST = RS == 1 && pad_step<NR, RAD, false, NS * RAD>(1) >= 0;
+  constexpr bool WR_CONST = RS == 1 && pad_step<NS, RAD, true, NS * RAD>(1) >= 0;
   C v[CP][NB][RAD];
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int j = t + b * T;
+    if constexpr (RD_CONST && CP == 1) {
+      const C* rb = buf + pad16(j) + col * CS;
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) {
-      if constexpr (VEC) {
-        const float4 q = *reinterpret_cast<const float4*>(&at(j + k * NR, 0));
-        v[0][b][k] = C{q.x, q.y};
-        v[CP - 1][b][k] = C{q.z, q.w};
-      } else {
+      for (int k = 0; k < RAD; ++k) v[0][b][k] = rb[pad_step<NR, RAD, false, NS * RAD>(k)];
+    } else {
 #pragma unroll
-        for (int cc = 0; cc < CP; ++cc) v[cc][b][k] = at(j + k * NR, cc);
+      for (int k = 0; k < RAD; ++k) {
+        if constexpr (VEC) {
+          const float4 q = *reinterpret_cast<const float4*>(&at(j + k * NR, 0));
+          v[0][b][k] = C{q.x, q.y};
+          v[CP - 1][b][k] = C{q.z, q.w};
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < CP; ++cc) v[cc][b][k] = at(j + k * NR, cc);
+        }
       }
     }
   }
@@ -169,14 +196,20 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
 #pragma unroll
     for (int cc = 0; cc < CP; ++cc) dft<RAD, INV>(v[cc][b]);
     const int base = (j - jm) * RAD + jm;
+    if constexpr (WR_CONST && CP == 1) {
+      C* wb = buf + pad16(base) + col * CS;
 #pragma unroll
-    for (int k = 0; k < RAD; ++k) {
-      if constexpr (VEC) {
-        *reinterpret_cast<float4*>(&at(base + k * NS, 0)) =
-            make_float4(v[0][b][k].x, v[0][b][k].y, v[CP - 1][b][k].x, v[CP - 1][b][k].y);
-      } else {
+      for (int k = 0; k < RAD; ++k) wb[pad_step<NS, RAD, true, NS * RAD>(k)] = v[0][b][k];
+    } else {
 #pragma unroll
-        for (int cc = 0; cc < CP; ++cc) at(base + k * NS, cc) = v[cc][b][k];
+      for (int k = 0; k < RAD; ++k) {
+        if constexpr (VEC) {
+          *reinterpret_cast<float4*>(&at(base + k * NS, 0)) =
+              make_float4(v[0][b][k].x, v[0][b][k].y, v[CP - 1][b][k].x, v[CP - 1][b][k].y);
+        } else {
+#pragma unroll
+          for (int cc = 0; cc < CP; ++cc) at(base + k * NS, cc) = v[cc][b][k];
+        }
       }
     }
   }
@@ -404,12 +437,13 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
   fft_column<C, H, false, 1, LD>(buf, h, t, tw);
   // X[k] = (Z[k] + conj Z[H-k]) / 2 + e^{-2 pi i k / N} (Z[k] - conj Z[H-k]) / (2i), k <= H
+  C* outb = out + row0 * P;
   auto untangle = [&](int hh, int k) {
     const C zk = buf[hh * LD + pad16(k % H)];
     const C zm = cconj(buf[hh * LD + pad16((H - k) % H)]);
     const C ev = C{R(0.5) * (zk.x + zm.x), R(0.5) * (zk.y + zm.y)};
     const C od = C{R(0.5) * (zk.y - zm.y), -R(0.5) * (zk.x - zm.x)};  // (zk - zm) / (2i)
-    out[(row0 + hh) * P + k] = cadd(ev, cmul(tu[k], od));
+    outb[hh * P + k] = cadd(ev, cmul(tu[k], od));
   };
   for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
     const int hh = e / H;
@@ -431,12 +465,13 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
   const long long row0 = (long long)blockIdx.x * ROWS;
   constexpr int THR = RowTile<R, N>::THREADS, PER = ROWS * H / THR;
   C vk[PER], vm[PER];
+  const C* inb = in + row0 * P;  // 32-bit offsets within the block's rows
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
     const int e = threadIdx.x + q * THR;
     const int h = e / H, k = e - h * H;
-    vk[q] = in[(row0 + h) * P + k];
-    vm[q] = in[(row0 + h) * P + (H - k)];
+    vk[q] = inb[h * P + k];
+    vm[q] = inb[h * P + (H - k)];
   }
 #pragma unroll
   for (int q = 0; q < PER; ++q) {
@@ -454,10 +489,10 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
   fft_column<C, H, true, 1, LD>(buf, h, t, tw);
-  C* outc = reinterpret_cast<C*>(out);
+  C* outc = reinterpret_cast<C*>(out) + row0 * H;
   for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
     const int hh = e / H, m = e - hh * H;
-    outc[(row0 + hh) * H + m] = buf[hh * LD + pad16(m)];
+    outc[e] = buf[hh * LD + pad16(m)];
   }
 }
 

@@ -172,34 +172,46 @@ __global__ void __launch_bounds__(256) k_paint(PState<R> s, R* __restrict__ rho,
   }
 }
 
-// kick with the force at the current positions, drift, paint the new position
+// kick with the force at the current position, drift, paint the new position
+template <typename R>
+__device__ __forceinline__ void kdk_one(PState<R> s, const R* __restrict__ F0, const R* __restrict__ F1,
+                                        const R* __restrict__ F2, R* __restrict__ rho, int M, R ckick, R cdrift,
+                                        R mass, long long j) {
+  int ix, iy, iz;
+  unpack(s.cell[j], ix, iy, iz);
+  R fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
+  const Corners c = corners(M, ix, iy, iz);
+  const R px = s.px[j] + ckick * gather(F0, c, fx, fy, fz);
+  const R py = s.py[j] + ckick * gather(F1, c, fx, fy, fz);
+  const R pz = s.pz[j] + ckick * gather(F2, c, fx, fy, fz);
+  // drift in cell units; carry the integer part into the cell index
+  R nx = fx + px * cdrift, ny = fy + py * cdrift, nz = fz + pz * cdrift;
+  R cx = floor(nx), cy = floor(ny), cz = floor(nz);
+  nx -= cx; ny -= cy; nz -= cz;
+  if (nx >= R(1)) { nx -= R(1); cx += R(1); }
+  if (ny >= R(1)) { ny -= R(1); cy += R(1); }
+  if (nz >= R(1)) { nz -= R(1); cz += R(1); }
+  ix = wrap32(ix + (int)cx, M);
+  iy = wrap32(iy + (int)cy, M);
+  iz = wrap32(iz + (int)cz, M);
+  s.px[j] = px; s.py[j] = py; s.pz[j] = pz;
+  s.cell[j] = pack(ix, iy, iz);
+  s.fx[j] = nx; s.fy[j] = ny; s.fz[j] = nz;
+  scatter(rho, corners(M, ix, iy, iz), nx, ny, nz, mass);
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_kdk_paint(PState<R> s, const R* __restrict__ F0, const R* __restrict__ F1,
                                                    const R* __restrict__ F2, R* __restrict__ rho, int M, R ckick,
                                                    R cdrift, R mass, long long np) {
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
-    int ix, iy, iz;
-    unpack(s.cell[j], ix, iy, iz);
-    R fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
-    const Corners c = corners(M, ix, iy, iz);
-    const R px = s.px[j] + ckick * gather(F0, c, fx, fy, fz);
-    const R py = s.py[j] + ckick * gather(F1, c, fx, fy, fz);
-    const R pz = s.pz[j] + ckick * gather(F2, c, fx, fy, fz);
-    // drift in cell units; carry the integer part into the cell index
-    R nx = fx + px * cdrift, ny = fy + py * cdrift, nz = fz + pz * cdrift;
-    R cx = floor(nx), cy = floor(ny), cz = floor(nz);
-    nx -= cx; ny -= cy; nz -= cz;
-    if (nx >= R(1)) { nx -= R(1); cx += R(1); }
-    if (ny >= R(1)) { ny -= R(1); cy += R(1); }
-    if (nz >= R(1)) { nz -= R(1); cz += R(1); }
-    ix = wrap32(ix + (int)cx, M);
-    iy = wrap32(iy + (int)cy, M);
-    iz = wrap32(iz + (int)cz, M);
-    s.px[j] = px; s.py[j] = py; s.pz[j] = pz;
-    s.cell[j] = pack(ix, iy, iz);
-    s.fx[j] = nx; s.fy[j] = ny; s.fz[j] = nz;
-    scatter(rho, corners(M, ix, iy, iz), nx, ny, nz, mass);
+  // two independent particles per iteration: their gathers and reductions overlap
+  const long long S = (long long)gridDim.x * blockDim.x;
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; j + S < np; j += 2 * S) {
+    kdk_one(s, F0, F1, F2, rho, M, ckick, cdrift, mass, j);
+    kdk_one(s, F0, F1, F2, rho, M, ckick, cdrift, mass, j + S);
   }
+  if (j < np) kdk_one(s, F0, F1, F2, rho, M, ckick, cdrift, mass, j);
 }
 
 // readout at the particles, written in lattice order (out[pid[j]])
