@@ -428,7 +428,7 @@ void adj_lpt2_src(const R* ls, R* const* d, R* const* out, long long n, cudaStre
 
 template <typename R>
 void adj_lens(const LensAdjArgs<R>& A, cudaStream_t st, Prof* pf) {
-  ProfScope ps(pf, KK_ADJ, st, A.np * (4.0 + 12.0 * sizeof(R)));
+  ProfScope ps(pf, KK_ADJ_LENS, st, A.np * (4.0 + 12.0 * sizeof(R)));
   k_lens_vjp<R><<<(int)std::min<long long>((A.np + 255) / 256, 152LL * 8), 256, 0, st>>>(A);
 }
 

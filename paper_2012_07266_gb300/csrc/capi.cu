@@ -83,6 +83,8 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
     L.adj_ckpt = a; a += (size_t)L.nck * L.state_bytes;
     L.adj_seg = a; a += (size_t)(std::min(k, cfg.nsteps) + 1) * L.state_bytes;
     L.adj_fseg = a; a += (size_t)(std::min(k, cfg.nsteps) + 1) * 3 * al(mesh);  // force meshes of the segment
+    // PGD meshes S(x_{i+1}) of the segment's lens steps, from the recompute
+    L.adj_sseg = a; a += cfg.pgd ? (size_t)std::min(k, cfg.nsteps) * 3 * al(mesh) : 0;
     L.adj_lx = a; a += al(3 * np * rs);
     L.adj_lp = a; a += al(3 * np * rs);
     L.adj_v = a; a += al(3 * np * rs);
@@ -274,7 +276,7 @@ cudaError_t upload_tables(pm_ctx* c) {
 // Paint is done by the caller into rho; this computes the force meshes (and
 // the PGD meshes when alpha_pgd is given) from rho.
 template <typename R>
-cudaError_t force_from_rho(pm_ctx* c, bool with_pgd, double alpha_pgd) {
+cudaError_t force_from_rho(pm_ctx* c, bool with_pgd, double alpha_pgd, size_t s_off = 0) {
   const pm_config& cfg = c->cfg;
   SpecParams sp = {};
   sp.err = timeout_ptr(c);
@@ -293,8 +295,10 @@ cudaError_t force_from_rho(pm_ctx* c, bool with_pgd, double alpha_pgd) {
   R* F = rp<R>(c, c->L.fmesh);
   for (int o = 0; o < 3; ++o) outs[o] = F + o * c->mesh_elems;
   if (with_pgd) {
-    R* S = rp<R>(c, c->L.smesh);
-    for (int o = 0; o < 3; ++o) outs[3 + o] = S + o * c->mesh_elems;
+    // PGD meshes: the context's, or (adjoint recompute) a segment slot
+    R* S = rp<R>(c, s_off ? s_off : c->L.smesh);
+    const size_t stride = s_off ? al(c->mesh_elems * c->rsz) / c->rsz : c->mesh_elems;
+    for (int o = 0; o < 3; ++o) outs[3 + o] = S + o * stride;
   }
   return spectral_apply<R>(rp<R>(c, c->L.rho), c->ws + c->L.cbuf, ub, outs, nout, c->M, c->P, sp, c->stream,
                            &c->prof);
@@ -493,6 +497,7 @@ AdjState<R> state_view(pm_ctx* c, size_t off) {
 
 size_t seg_off(pm_ctx* c, int j) { return c->L.adj_seg + (size_t)j * c->L.state_bytes; }
 size_t fseg_off(pm_ctx* c, int j) { return c->L.adj_fseg + (size_t)j * 3 * al(c->mesh_elems * c->rsz); }
+size_t sseg_off(pm_ctx* c, int j) { return c->L.adj_sseg + (size_t)j * 3 * al(c->mesh_elems * c->rsz); }
 
 // keep the current force meshes as segment entry j
 cudaError_t save_force(pm_ctx* c, int j) {
@@ -583,8 +588,6 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
   for (int q = 0; q < cfg.n_zs; ++q) adj_dsum(lam + q * npix2, npix2, acc + 4 * n + q, s, pf);
   R* F = rp<R>(c, c->L.fmesh);
   R* Fm[3] = {F, F + c->mesh_elems, F + 2 * c->mesh_elems};
-  R* S = rp<R>(c, c->L.smesh);
-  R* Sm[3] = {S, S + c->mesh_elems, S + 2 * c->mesh_elems};
   const double vp = std::pow(cfg.box / c->nc, 3.0);
   const double dth = cfg.map_fov_deg * M_PI / 180.0 / cfg.map_npix;
   const double wpref_p = 1.5 * (cfg.omega_m + c->adj_h) / (kCoverH0 * kCoverH0) * vp / (dth * dth);
@@ -610,7 +613,10 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
       R* rho = rp<R>(c, c->L.rho);
       if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, s))) return PM_ERR_CUDA;
       if ((e = launch_kdk_paint<R>(c, rho, c->kick[i], c->drift[i]))) return PM_ERR_CUDA;
-      if ((e = force_from_rho<R>(c, false, 0.0))) return PM_ERR_CUDA;
+      // lens steps with PGD: S(x_{i+1}) comes with the force, kept for the reverse sweep
+      const bool pg_i = cfg.pgd && shell_active(c, i);
+      if ((e = force_from_rho<R>(c, pg_i, pg_i ? pgd_alpha(c, i) : 0.0, pg_i ? sseg_off(c, i - i0) : 0)))
+        return PM_ERR_CUDA;
       if ((e = save_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
       if (i + 1 < i1 && (e = save_force(c, i - i0 + 1))) return PM_ERR_CUDA;  // F(x_{i+1}) for kick i+1
     }
@@ -619,10 +625,11 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
       const AdjState<R> st1 = state_view<R>(c, seg_off(c, i - i0 + 1));  // x_{i+1}, p_{i+1/2}
       if (shell_active(c, i)) {
         const bool pg = cfg.pgd != 0;
-        if (pg) {
-          if ((e = load_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
-          if ((e = force_at_working<R>(c, true, pgd_alpha(c, i)))) return PM_ERR_CUDA;
-        }
+        // S(x_{i+1}) from the segment recompute
+        R* Sseg = rp<R>(c, sseg_off(c, i - i0));
+        const size_t sstride = al(c->mesh_elems * c->rsz) / c->rsz;
+        R* Sm[3] = {Sseg, Sseg + sstride, Sseg + 2 * sstride};
+        c->s_at = pg ? sseg_off(c, i - i0) : 0;
         LensShell sh = make_shell(c, i, c->cosmo);
         const std::vector<Replica> reps = shell_replicas(c, std::sqrt(sh.chi_lo2), std::sqrt(sh.chi_hi2));
         LensAdjArgs<R> A;
@@ -659,7 +666,7 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
         A.vS = pg ? vS : nullptr;
         if (pg && (e = cudaMemsetAsync(vS, 0, np3 * c->rsz, s))) return PM_ERR_CUDA;
         // the working state holds x_{i+1} for the dot passes
-        if (!pg && (e = load_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
+        if ((e = load_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
         LensShell shp = make_shell(c, i, c->cos_p), shm = make_shell(c, i, c->cos_m);
         for (size_t b = 0; b < reps.size(); b += kMaxReplicas) {
           A.nrep = (int)std::min<size_t>(kMaxReplicas, reps.size() - b);
@@ -707,7 +714,7 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
     R* outs[9];
     for (int q = 0; q < 9; ++q) outs[q] = field(q);
     cudaError_t ee = spectral_apply<R>(rp<R>(c, c->L.adj_noise), c->ws + c->L.ic_cbuf, ub, outs, two ? 9 : 3, c->nc,
-                                       c->Pc, sp, s, pf, KK_ADJ);
+                                       c->Pc, sp, s, pf, KK_ADJ_FFT);
     if (ee || !two) return ee;
     R* d[6];
     for (int q = 0; q < 6; ++q) d[q] = field(3 + q);
@@ -715,7 +722,7 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
     SpecParams sp2 = sp;
     sp2.op = OP_GRAD_NEG;
     R* o2[3] = {field(10), field(11), field(12)};
-    return spectral_apply<R>(field(9), c->ws + c->L.ic_cbuf, ub, o2, 3, c->nc, c->Pc, sp2, s, pf, KK_ADJ);
+    return spectral_apply<R>(field(9), c->ws + c->L.ic_cbuf, ub, o2, 3, c->nc, c->Pc, sp2, s, pf, KK_ADJ_FFT);
   };
   const double cpl = c->M / cfg.box;
   const double a0 = c->a[0];
@@ -958,6 +965,7 @@ pm_status pm_vjp(pm_ctx* c, const double* d_dL_dkappa, double* d_dL_dnoise, doub
   if (!c->ic_done || c->next_step != c->cfg.nsteps || c->projected != c->cfg.nsteps - 1 || c->vjp_state_lost)
     return PM_ERR_STATE;
   pm_status st = PM_DISPATCH(c, do_vjp, c, d_dL_dkappa, d_dL_dnoise, h_dL_dparams);
+  c->s_at = 0;
   // the reverse sweep reuses the particle arrays: the forward state is gone
   c->last_stepped = -1;
   c->vjp_state_lost = 1;

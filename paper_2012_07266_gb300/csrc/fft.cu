@@ -128,18 +128,18 @@ struct Launch {
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < nin && !e; ++i) {
       C* u = reinterpret_cast<C*>(ubufs[i]);
-      x_fwd(real_in[i], u, P, s, pf, KK_ADJ);
-      e = y(u, P, false, s, pf, KK_ADJ, sp.err);
+      x_fwd(real_in[i], u, P, s, pf, KK_ADJ_FFT);
+      e = y(u, P, false, s, pf, KK_ADJ_FFT, sp.err);
     }
     if (e) return e;
     C* c = reinterpret_cast<C*>(cbuf);
     {
-      ProfScope ps(pf, KK_ADJ, s, (nin + 1) * CB);
+      ProfScope ps(pf, KK_ADJ_FFT, s, (nin + 1) * CB);
       dim3 g((N / 2 + 1 + ZTile<R, N>::W - 1) / ZTile<R, N>::W, N);
       k_zpass_combine<R, N><<<g, ZTile<R, N>::THREADS, smem_z(), s>>>(ip, nin, first, c, P, sp);
     }
-    if ((e = y(c, P, true, s, pf, KK_ADJ, sp.err))) return e;
-    x_inv(c, real_out, P, s, pf, KK_ADJ);
+    if ((e = y(c, P, true, s, pf, KK_ADJ_FFT, sp.err))) return e;
+    x_inv(c, real_out, P, s, pf, KK_ADJ_FFT);
     return cudaGetLastError();
   }
 

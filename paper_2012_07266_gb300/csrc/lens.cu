@@ -228,7 +228,7 @@ cudaError_t launch_lens_dot(pm_ctx* c, const LensShell& sh, int use_pgd, const d
   A.acc = acc;
   long long blocks = (c->np + 255) / 256;
   if (blocks > 152LL * 8) blocks = 152LL * 8;
-  ProfScope ps(&c->prof, KK_ADJ, c->stream, c->np * (4.0 + 6.0 * sizeof(R)));
+  ProfScope ps(&c->prof, KK_ADJ_LENS, c->stream, c->np * (4.0 + 6.0 * sizeof(R)));
   k_lens<R><<<(int)blocks, 256, 0, c->stream>>>(A);
   return cudaGetLastError();
 }
@@ -241,8 +241,10 @@ static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs
   A.fx = f; A.fy = f + c->np; A.fz = f + 2 * c->np;
   A.px = p; A.py = p + c->np; A.pz = p + 2 * c->np;
   if (use_pgd) {
-    const R* S = reinterpret_cast<const R*>(c->ws + c->L.smesh);
-    A.S0 = S; A.S1 = S + c->mesh_elems; A.S2 = S + 2 * c->mesh_elems;
+    // the context's PGD meshes, or the adjoint's segment slot (256-byte aligned meshes)
+    const R* S = reinterpret_cast<const R*>(c->ws + (c->s_at ? c->s_at : c->L.smesh));
+    const size_t stride = c->s_at ? (c->mesh_elems * sizeof(R) + 255) / 256 * 256 / sizeof(R) : c->mesh_elems;
+    A.S0 = S; A.S1 = S + stride; A.S2 = S + 2 * stride;
   } else {
     A.S0 = A.S1 = A.S2 = nullptr;
   }
