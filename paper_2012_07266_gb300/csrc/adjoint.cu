@@ -18,6 +18,7 @@
 #include <cmath>
 
 #include "adjoint.h"
+#include "cic.cuh"
 
 namespace pmlens {
 
@@ -73,6 +74,8 @@ __device__ __forceinline__ void cic_offsets(const int* i, int M, long long* o) {
 }
 
 // --------------------------------------------------------------- kernels
+// paint three cotangent components (the transpose of a CIC readout of three
+// meshes); x-adjacent corners share one vector reduction (FP32)
 template <typename R>
 __global__ void k_paint_weights(AdjState<R> s, const R* __restrict__ v0, const R* __restrict__ v1,
                                 const R* __restrict__ v2, R* __restrict__ m0, R* __restrict__ m1,
@@ -80,18 +83,11 @@ __global__ void k_paint_weights(AdjState<R> s, const R* __restrict__ v0, const R
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
     int i[3];
     unpack3(s.cell[j], i);
-    const R f[3] = {s.fx[j], s.fy[j], s.fz[j]};
-    long long o[8];
-    cic_offsets<R>(i, M, o);
-    const R a = v0[j], b = v1[j], c = v2[j];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const R w = ((k & 1) ? f[0] : R(1) - f[0]) * (((k >> 1) & 1) ? f[1] : R(1) - f[1]) *
-                  ((k >> 2) ? f[2] : R(1) - f[2]);
-      atomicAdd(m0 + o[k], w * a);
-      atomicAdd(m1 + o[k], w * b);
-      atomicAdd(m2 + o[k], w * c);
-    }
+    const Corners c = corners(M, i[0], i[1], i[2]);
+    const R fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
+    scatter(m0, c, fx, fy, fz, v0[j]);
+    scatter(m1, c, fx, fy, fz, v1[j]);
+    scatter(m2, c, fx, fy, fz, v2[j]);
   }
 }
 
@@ -107,8 +103,10 @@ __global__ void k_readout_grad(AdjState<R> s, const R* __restrict__ m0, const R*
     int i[3];
     unpack3(s.cell[j], i);
     const R f[3] = {s.fx[j], s.fy[j], s.fz[j]};
-    long long o[8];
-    cic_offsets<R>(i, M, o);
+    const Corners cc = corners(M, i[0], i[1], i[2]);
+    // corner k = (dx, dy, dz) = (k & 1, k >> 1 & 1, k >> 2), 32-bit offsets
+    const unsigned o[8] = {cc.r00 + cc.x0, cc.r00 + cc.x1, cc.r01 + cc.x0, cc.r01 + cc.x1,
+                           cc.r10 + cc.x0, cc.r10 + cc.x1, cc.r11 + cc.x0, cc.r11 + cc.x1};
     const R v[3] = {v0[j], v1[j], v2[j]};
     R g[3] = {R(0), R(0), R(0)};
     R val[3] = {R(0), R(0), R(0)};
