@@ -107,6 +107,10 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
 template <typename R>
 R* rp(pm_ctx* c, size_t off) { return reinterpret_cast<R*>(c->ws + off); }
 
+size_t seg_off(pm_ctx* c, int j);
+size_t fseg_off(pm_ctx* c, int j);
+size_t sseg_off(pm_ctx* c, int j);
+
 size_t cmesh_bytes(pm_ctx* c) { return (size_t)c->M * c->M * c->P * 2 * c->rsz; }
 size_t cgrid_bytes(pm_ctx* c) { return (size_t)c->nc * c->nc * c->Pc * 2 * c->rsz; }
 
@@ -276,7 +280,7 @@ cudaError_t upload_tables(pm_ctx* c) {
 // Paint is done by the caller into rho; this computes the force meshes (and
 // the PGD meshes when alpha_pgd is given) from rho.
 template <typename R>
-cudaError_t force_from_rho(pm_ctx* c, bool with_pgd, double alpha_pgd, size_t s_off = 0) {
+cudaError_t force_from_rho(pm_ctx* c, bool with_pgd, double alpha_pgd, size_t s_off = 0, size_t f_off = 0) {
   const pm_config& cfg = c->cfg;
   SpecParams sp = {};
   sp.err = timeout_ptr(c);
@@ -292,13 +296,13 @@ cudaError_t force_from_rho(pm_ctx* c, bool with_pgd, double alpha_pgd, size_t s_
   void* ub[6];
   R* outs[6];
   for (int o = 0; o < nout; ++o) ub[o] = c->ws + c->L.ubuf + o * al(cmesh_bytes(c));
-  R* F = rp<R>(c, c->L.fmesh);
+  // force (and PGD) meshes: the context's, or adjoint segment slots (three meshes of
+  // mesh_elems each: the mesh bytes of every supported size are a multiple of 256)
+  R* F = rp<R>(c, f_off ? f_off : c->L.fmesh);
   for (int o = 0; o < 3; ++o) outs[o] = F + o * c->mesh_elems;
   if (with_pgd) {
-    // PGD meshes: the context's, or (adjoint recompute) a segment slot
     R* S = rp<R>(c, s_off ? s_off : c->L.smesh);
-    const size_t stride = s_off ? al(c->mesh_elems * c->rsz) / c->rsz : c->mesh_elems;
-    for (int o = 0; o < 3; ++o) outs[3 + o] = S + o * stride;
+    for (int o = 0; o < 3; ++o) outs[3 + o] = S + o * c->mesh_elems;
   }
   return spectral_apply<R>(rp<R>(c, c->L.rho), c->ws + c->L.cbuf, ub, outs, nout, c->M, c->P, sp, c->stream,
                            &c->prof);
@@ -352,7 +356,11 @@ pm_status do_ic(pm_ctx* c, const double* d_noise) {
   R* rho = rp<R>(c, c->L.rho);
   if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, s))) return PM_ERR_CUDA;
   if ((e = launch_paint<R>(c, rho))) return PM_ERR_CUDA;
-  if ((e = force_from_rho<R>(c, false, 0.0))) return PM_ERR_CUDA;
+  // resident adjoint: F(x_0) goes straight into segment slot 0
+  const size_t f_off = adj_resident(c->cfg) ? fseg_off(c, 0) : 0;
+  if ((e = force_from_rho<R>(c, false, 0.0, 0, f_off))) return PM_ERR_CUDA;
+  c->f_at = f_off;
+  c->s_at = 0;
   return PM_OK;
 }
 
@@ -363,7 +371,13 @@ pm_status do_step(pm_ctx* c, int i) {
   if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, c->stream))) return PM_ERR_CUDA;
   if ((e = launch_kdk_paint<R>(c, rho, c->kick[i], c->drift[i]))) return PM_ERR_CUDA;
   const bool pgd = c->cfg.pgd && shell_active(c, i);
-  if ((e = force_from_rho<R>(c, pgd, pgd ? pgd_alpha(c, i) : 0.0))) return PM_ERR_CUDA;
+  // resident adjoint: F(x_{i+1}) and S(x_{i+1}) land in the step's segment slots
+  const bool res = adj_resident(c->cfg);
+  const size_t f_off = res && i + 1 < c->cfg.nsteps ? fseg_off(c, i + 1) : 0;
+  const size_t s_off = res && pgd ? sseg_off(c, i) : 0;
+  if ((e = force_from_rho<R>(c, pgd, pgd ? pgd_alpha(c, i) : 0.0, s_off, f_off))) return PM_ERR_CUDA;
+  c->f_at = f_off;
+  c->s_at = s_off;
   c->pgd_valid = pgd;
   return PM_OK;
 }
@@ -593,6 +607,7 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
   const double wpref_p = 1.5 * (cfg.omega_m + c->adj_h) / (kCoverH0 * kCoverH0) * vp / (dth * dth);
   const double wpref_m = 1.5 * (cfg.omega_m - c->adj_h) / (kCoverH0 * kCoverH0) * vp / (dth * dth);
   const int nck = c->L.nck;
+  const bool resident = adj_resident(cfg) && (int)c->sorted_after.size() == n;
   for (int seg = nck - 1; seg >= 0; --seg) {
     const int i0 = seg * k, i1 = std::min(n, i0 + k);
     if (seg < nck - 1) {
@@ -605,6 +620,8 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
       }
     }
     // recompute the segment forward from its checkpoint, keeping every state
+    // (resident mode: the forward already kept them)
+    if (!resident) {
     if ((e = load_state(c, ckpt_off(c, seg)))) return PM_ERR_CUDA;
     if ((e = force_at_working<R>(c, false, 0.0))) return PM_ERR_CUDA;
     if ((e = save_state(c, seg_off(c, 0)))) return PM_ERR_CUDA;
@@ -619,6 +636,7 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
         return PM_ERR_CUDA;
       if ((e = save_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
       if (i + 1 < i1 && (e = save_force(c, i - i0 + 1))) return PM_ERR_CUDA;  // F(x_{i+1}) for kick i+1
+    }
     }
     // reverse sweep through the segment
     for (int i = i1 - 1; i >= i0; --i) {
@@ -687,6 +705,15 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
       // drift x_{i+1} = x_i + drift_i p_{i+1/2}
       adj_dot<R>(lx, st1.px, np3, acc + n + i, s, pf);
       adj_axpy<R>(lp, lx, c->drift[i], np3, s, pf);
+      if (resident && c->sorted_after[i]) {
+        // the state was re-sorted after step i: bring the adjoint to x_i's particle order
+        const uint32_t* pid1 = state_pid(c, seg_off(c, i + 1));
+        const uint32_t* pid0 = state_pid(c, seg_off(c, i));
+        for (R* a : {lx, lp}) {
+          if (launch_unpermute3<R>(c, a, pid1, v)) return PM_ERR_CUDA;
+          if (launch_permute3<R>(c, v, pid0, a)) return PM_ERR_CUDA;
+        }
+      }
       // kick p_{i+1/2} = p_{i-1/2} + kick_i F(x_i)
       const AdjState<R> st0 = state_view<R>(c, seg_off(c, i - i0));
       R* Fi = rp<R>(c, fseg_off(c, i - i0));  // F(x_i), kept by the segment recompute
@@ -810,6 +837,7 @@ pm_status do_set_particles(pm_ctx* c, const double* x, const double* p, int ns) 
   if (launch_paint<R>(c, rho)) return PM_ERR_CUDA;
   const bool pgd = ns > 0 && c->cfg.pgd && shell_active(c, ns - 1);
   if (force_from_rho<R>(c, pgd, pgd ? pgd_alpha(c, ns - 1) : 0.0)) return PM_ERR_CUDA;
+  c->f_at = c->s_at = 0;
   c->pgd_valid = pgd;
   return PM_OK;
 }
@@ -911,6 +939,8 @@ pm_status pm_ic(pm_ctx* c, const double* d_noise) {
                         ? launch_convert_in<double>(d_noise, rp<double>(c, c->L.adj_noise), g, c->stream, &c->prof)
                         : launch_convert_in<float>(d_noise, rp<float>(c, c->L.adj_noise), g, c->stream, &c->prof);
     if (e || save_state(c, ckpt_off(c, 0))) return PM_ERR_CUDA;
+    if (adj_resident(c->cfg) && save_state(c, seg_off(c, 0))) return PM_ERR_CUDA;
+    c->sorted_after.assign(c->cfg.nsteps, 0);
   }
   c->ic_done = 1;
   c->next_step = 0;
@@ -930,9 +960,15 @@ pm_status pm_step(pm_ctx* c, int32_t i) {
   // restore spatial locality of the particle order (at checkpoint boundaries when the
   // adjoint is on, so that every checkpoint segment keeps one particle order)
   const int se = sort_every(c->cfg);
-  if ((i + 1) % se == 0 && i + 1 < c->cfg.nsteps) {
+  const bool sorted = (i + 1) % se == 0 && i + 1 < c->cfg.nsteps;
+  if (sorted) {
     cudaError_t e = c->prec == PM_FP64 ? sort_particles<double>(c) : sort_particles<float>(c);
     if (e) return PM_ERR_CUDA;
+  }
+  if (adj_resident(c->cfg)) {
+    // keep x_{i+1}, p_{i+1/2} in the order step i+1 uses
+    if (save_state(c, seg_off(c, i + 1))) return PM_ERR_CUDA;
+    if ((int)c->sorted_after.size() == c->cfg.nsteps) c->sorted_after[i] = sorted ? 1 : 0;
   }
   const int k = c->cfg.ckpt_every;
   if (k > 0 && (i + 1) % k == 0 && i + 1 < c->cfg.nsteps) {
@@ -966,6 +1002,7 @@ pm_status pm_vjp(pm_ctx* c, const double* d_dL_dkappa, double* d_dL_dnoise, doub
     return PM_ERR_STATE;
   pm_status st = PM_DISPATCH(c, do_vjp, c, d_dL_dkappa, d_dL_dnoise, h_dL_dparams);
   c->s_at = 0;
+  c->f_at = 0;
   // the reverse sweep reuses the particle arrays: the forward state is gone
   c->last_stepped = -1;
   c->vjp_state_lost = 1;
@@ -1020,13 +1057,13 @@ pm_status pm_set_particles(pm_ctx* c, const double* d_x, const double* d_p, int3
 pm_status pm_get_forces(pm_ctx* c, double* d_f) {
   if (!c || !d_f) return PM_ERR_ARG;
   if (!c->ic_done) return PM_ERR_STATE;
-  return PM_DISPATCH(c, do_readout, c, c->L.fmesh, d_f);
+  return PM_DISPATCH(c, do_readout, c, fmesh_at(c), d_f);
 }
 
 pm_status pm_get_pgd(pm_ctx* c, double* d_s) {
   if (!c || !d_s) return PM_ERR_ARG;
   if (!c->ic_done || !c->pgd_valid) return PM_ERR_STATE;
-  return PM_DISPATCH(c, do_readout, c, c->L.smesh, d_s);
+  return PM_DISPATCH(c, do_readout, c, smesh_at(c), d_s);
 }
 
 pm_status pm_fft_r2c(pm_ctx* c, const double* d_in, double* d_out) {

@@ -241,10 +241,9 @@ static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs
   A.fx = f; A.fy = f + c->np; A.fz = f + 2 * c->np;
   A.px = p; A.py = p + c->np; A.pz = p + 2 * c->np;
   if (use_pgd) {
-    // the context's PGD meshes, or the adjoint's segment slot (256-byte aligned meshes)
-    const R* S = reinterpret_cast<const R*>(c->ws + (c->s_at ? c->s_at : c->L.smesh));
-    const size_t stride = c->s_at ? (c->mesh_elems * sizeof(R) + 255) / 256 * 256 / sizeof(R) : c->mesh_elems;
-    A.S0 = S; A.S1 = S + stride; A.S2 = S + 2 * stride;
+    // the context's PGD meshes, or an adjoint segment slot
+    const R* S = reinterpret_cast<const R*>(c->ws + smesh_at(c));
+    A.S0 = S; A.S1 = S + c->mesh_elems; A.S2 = S + 2 * c->mesh_elems;
   } else {
     A.S0 = A.S1 = A.S2 = nullptr;
   }

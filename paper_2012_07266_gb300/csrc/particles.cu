@@ -247,7 +247,7 @@ cudaError_t launch_paint(pm_ctx* c, R* rho) {
 template <typename R>
 cudaError_t launch_kdk_paint(pm_ctx* c, R* rho, double ckick, double cdrift) {
   const double mass = std::pow((double)c->M / c->nc, 3.0);
-  R* F = reinterpret_cast<R*>(c->ws + c->L.fmesh);
+  R* F = reinterpret_cast<R*>(c->ws + fmesh_at(c));  // F(x_i)
   // state read + written, three force meshes gathered, density written
   ProfScope ps(&c->prof, KK_KDK_PAINT, c->stream,
                2.0 * c->np * (4.0 + 6.0 * sizeof(R)) + 4.0 * c->mesh_elems * (double)sizeof(R));

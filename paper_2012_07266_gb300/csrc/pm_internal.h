@@ -143,6 +143,8 @@ struct pm_ctx {
   int projected;     // last projected shell
   int pgd_valid;     // PGD meshes valid for last_stepped
   size_t s_at = 0;   // workspace offset of the PGD meshes the lens kernels read (0: L.smesh)
+  size_t f_at = 0;   // workspace offset of the current force meshes (0: L.fmesh)
+  std::vector<char> sorted_after;  // resident adjoint: the state was re-sorted at the end of step i
   int ic_done;
   int vjp_state_lost;  // 1: checkpoints do not describe the current run
   pmlens::Prof prof;
@@ -213,7 +215,13 @@ cudaError_t launch_unpermute3(pm_ctx* c, const R* src, const uint32_t* pid, R* d
 template <typename R>
 cudaError_t launch_permute3(pm_ctx* c, const R* src, const uint32_t* pid, R* dst);
 size_t sort_scratch_bytes(int M);
-inline int sort_every(const pm_config& cfg) { return cfg.ckpt_every > 0 ? cfg.ckpt_every : 4; }
+// Resident adjoint (ckpt_every >= nsteps): the forward keeps every step's state, force meshes and
+// PGD meshes in the workspace, and the reverse sweep recomputes nothing.
+inline bool adj_resident(const pm_config& cfg) { return cfg.ckpt_every > 0 && cfg.ckpt_every >= cfg.nsteps; }
+// re-sort every 4 steps; with checkpoint segments, only at segment boundaries
+inline int sort_every(const pm_config& cfg) {
+  return cfg.ckpt_every > 0 && cfg.ckpt_every < cfg.nsteps ? cfg.ckpt_every : 4;
+}
 
 // lensing (lens.cu)
 template <typename R>
@@ -245,5 +253,7 @@ inline const R* chi_table(pm_ctx* c, int id) {
 }
 inline int* flags_ptr(pm_ctx* c) { return reinterpret_cast<int*>(c->ws + c->L.flags); }
 inline int* timeout_ptr(pm_ctx* c) { return flags_ptr(c) + 1; }
+inline size_t fmesh_at(const pm_ctx* c) { return c->f_at ? c->f_at : c->L.fmesh; }
+inline size_t smesh_at(const pm_ctx* c) { return c->s_at ? c->s_at : c->L.smesh; }
 
 }  // namespace pmlens

@@ -57,3 +57,5 @@ def test_config_validation_returns_errors_before_device_work(L):
     assert so.pm_workspace_size(C.byref(bad), C.byref(n)) == 1
     assert so.pm_step(None, 0) == 1 and so.kappa_maps(None, None) == 1
     assert so.pm_strerror(5) == b"entry point called out of order"
+    assert so.pm_strerror(7) == b"device-side wait for a bulk copy timed out"
+    assert L.STATUS[7] == "PM_ERR_TIMEOUT"

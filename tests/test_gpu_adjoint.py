@@ -1,6 +1,9 @@
 """GPU reverse-mode derivative (pm_vjp) against the oracle's FP64 adjoint and
 against finite differences of the GPU forward model, through the C ABI.
 
+Checkpointed (ckpt_every < nsteps: segments recomputed from checkpoints) and
+resident (ckpt_every >= nsteps: nothing recomputed) reverse sweeps.
+
 Tolerances: the noise gradient matches the oracle to relative L2 1e-6 on the
 FP64 path and 2e-3 on the FP32 path (FP32 particle state and meshes);
 dL/dsigma_8 to 1e-6 / 2e-3; dL/dOmega_m to 1e-6 / 5e-3, both sides taking the
@@ -39,6 +42,11 @@ CASES = [
     (0, dict(), 2e-3, 5e-3),
     (1, dict(lpt_order=2, pgd=1, zs=(0.8, 1.0), ckpt_every=4), 1e-6, 1e-6),
     (0, dict(lpt_order=2, pgd=1, zs=(0.8, 1.0), ckpt_every=4), 2e-3, 5e-3),
+    # resident adjoint (ckpt_every >= nsteps): every state, force and PGD mesh kept by the forward,
+    # no recompute; the state is re-sorted after step 3, inside the single segment
+    (1, dict(lpt_order=2, pgd=1, zs=(0.8, 1.0), ckpt_every=6), 1e-6, 1e-6),
+    (0, dict(lpt_order=2, pgd=1, zs=(0.8, 1.0), ckpt_every=100), 2e-3, 5e-3),
+    (0, dict(ckpt_every=6), 2e-3, 5e-3),
 ]
 
 
