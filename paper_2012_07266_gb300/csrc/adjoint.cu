@@ -80,7 +80,7 @@ template <typename R>
 __global__ void k_paint_weights(AdjState<R> s, const R* __restrict__ v0, const R* __restrict__ v1,
                                 const R* __restrict__ v2, R* __restrict__ m0, R* __restrict__ m1,
                                 R* __restrict__ m2, int M, long long np) {
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+  auto one = [&](long long j) {
     int i[3];
     unpack3(s.cell[j], i);
     const Corners c = corners(M, i[0], i[1], i[2]);
@@ -88,7 +88,15 @@ __global__ void k_paint_weights(AdjState<R> s, const R* __restrict__ v0, const R
     scatter(m0, c, fx, fy, fz, v0[j]);
     scatter(m1, c, fx, fy, fz, v1[j]);
     scatter(m2, c, fx, fy, fz, v2[j]);
+  };
+  // two independent particles per iteration (overlapping their loads and reductions)
+  const long long S = (long long)gridDim.x * blockDim.x;
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; j + S < np; j += 2 * S) {
+    one(j);
+    one(j + S);
   }
+  if (j < np) one(j);
 }
 
 // lam_x += sum_c v_c grad readout(mesh_c) + mass grad readout(phi); optional

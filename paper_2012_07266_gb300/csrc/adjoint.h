@@ -63,9 +63,18 @@ void adj_lpt2_src(const R* ls, R* const* d, R* const* out, long long n, cudaStre
 template <typename R>
 void adj_lens(const LensAdjArgs<R>& A, cudaStream_t st, Prof* pf);
 
-// lens kernel in "dot" mode: acc += sum lam * (this shell's map increment)
+// One cosmology of a lens dot product: chi tables (TabId), source distances,
+// weight prefactor, the shell's D1(a_{i+1}) and g_p(a_{i+1/2}), accumulator.
+struct LensDotVar {
+  int tab_d1, tab_inva;
+  const double* chi_s;
+  double wpref, d1_next, gp_half;
+  double* acc;
+};
+// lens kernel in "dot" mode for two cosmologies on the selection (shell bounds,
+// replicas) of `sel`: a.acc += sum lam * (map increment under a), same for b
 template <typename R>
-cudaError_t launch_lens_dot(pm_ctx* c, const LensShell& sh, int use_pgd, const double* lam, int tab_d1,
-                            int tab_inva, const double* chi_s, double wpref, double* acc);
+cudaError_t launch_lens_dot2(pm_ctx* c, const LensShell& sel, int use_pgd, const double* lam, const LensDotVar& a,
+                             const LensDotVar& b);
 
 }  // namespace pmlens

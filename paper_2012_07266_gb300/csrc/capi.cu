@@ -692,10 +692,11 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
           adj_lens<R>(A, s, pf);
           shp.nrep = shm.nrep = A.nrep;
           for (int q = 0; q < A.nrep; ++q) shp.rep[q] = shm.rep[q] = A.rep[q];
-          if (launch_lens_dot<R>(c, shp, pg, lam, T_D1P, T_INVAP, c->chi_s_p.data(), wpref_p, acc + 2 * n + i))
-            return PM_ERR_CUDA;
-          if (launch_lens_dot<R>(c, shm, pg, lam, T_D1M, T_INVAM, c->chi_s_m.data(), wpref_m, acc + 3 * n + i))
-            return PM_ERR_CUDA;
+          const LensDotVar vp_ = {T_D1P, T_INVAP, c->chi_s_p.data(), wpref_p, shp.d1_next, shp.gp_half,
+                                  acc + 2 * n + i};
+          const LensDotVar vm_ = {T_D1M, T_INVAM, c->chi_s_m.data(), wpref_m, shm.d1_next, shm.gp_half,
+                                  acc + 3 * n + i};
+          if (launch_lens_dot2<R>(c, shp, pg, lam, vp_, vm_)) return PM_ERR_CUDA;
         }
         if (pg) {
           // PGD transpose at x_{i+1} (meshes of S still current)

@@ -15,6 +15,19 @@ namespace pmlens {
 
 namespace {
 
+// Cosmology-dependent part of a projection: growth and 1/a tables, source
+// distances, weight prefactor, the shell's D1(a_{i+1}) and 1/g_p(a_{i+1/2}), and
+// (dot mode) where the dot product accumulates.
+template <typename R>
+struct LensVar {
+  const R* tab_d1;    // D1(a(chi)) on a uniform chi grid (path precision)
+  const R* tab_inva;  // 1 / a(chi)
+  double chi_s[PM_MAX_ZS];
+  double wpref;       // (3/2) Om (H0/c)^2 V_p / Omega_pix
+  double d1_next, inv_gp_half;
+  double* acc;
+};
+
 template <typename R>
 struct LensArgs {
   const uint32_t* cell;
@@ -28,17 +41,12 @@ struct LensArgs {
   double tan_half;  // tan of half the field of view plus one pixel
   double margin;    // bound on the sub-evolution + PGD displacement (Mpc/h)
   int npix, nzs, sub;
-  double chi_s[PM_MAX_ZS];
-  double wpref;            // (3/2) Om (H0/c)^2 V_p / Omega_pix
-  double d1_next, inv_gp_half;
   double tab_hinv;
   int tab_n;
-  const R* tab_d1;         // D1(a(chi)) on a uniform chi grid (path precision)
-  const R* tab_inva;       // 1 / a(chi)
+  LensVar<R> var[2];  // var[0]; dot mode may add a second cosmology (var[1]) on the same selection
   double* maps;
   int* flag;
-  const double* lam;  // when set: accumulate sum(lam * increment) into *acc instead of the maps
-  double* acc;
+  const double* lam;  // when set: accumulate sum(lam * increment) into var[v].acc instead of the maps
   int nrep;
   Replica rep[kMaxReplicas];
 };
@@ -88,12 +96,16 @@ __device__ __forceinline__ R gather3(const R* __restrict__ m, int M, int ix, int
 }
 
 // Geometry runs in the path's precision R (FP32 fast path, FP64 plain path).
-template <typename R>
+// NV cosmology variants share the particle read, the replica transform, the
+// shell selection and the PGD gather (NV = 2: the Omega_m +/- h dot products).
+template <typename R, int NV>
 __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
   const R cell_len = (R)A.cell_len, lo2 = (R)A.chi_lo2, hi2 = (R)A.chi_hi2;
   const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
   const R tan_half = (R)A.tan_half, margin = (R)A.margin;
-  R dot = R(0);
+  R dot[NV];
+#pragma unroll
+  for (int vi = 0; vi < NV; ++vi) dot[vi] = R(0);
   for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.np;
        j += (long long)gridDim.x * blockDim.x) {
     const uint32_t c = A.cell[j];
@@ -140,51 +152,63 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
           sr[d] = (rp.flip >> d & 1) ? -v : v;
         }
       }
-      if (A.sub) {
-        const R t = interp<R>(A.tab_d1, A.tab_n, (R)A.tab_hinv, sqrt(chi2));
-        const R dt = (t - (R)A.d1_next) * (R)A.inv_gp_half * cell_len;
+      const R chi = A.sub ? sqrt(chi2) : R(0);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) r[d] += pr[d] * dt;
-      }
-      if (A.S0) {
+      for (int vi = 0; vi < NV; ++vi) {
+        const LensVar<R>& V = A.var[vi];
+        R q[3] = {r[0], r[1], r[2]};
+        if (A.sub) {
+          const R t = interp<R>(V.tab_d1, A.tab_n, (R)A.tab_hinv, chi);
+          const R dt = (t - (R)V.d1_next) * (R)V.inv_gp_half * cell_len;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) r[d] += sr[d] * cell_len;
-      }
-      if (!(r[2] > R(0))) continue;
-      const R chic = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-      const R inz = R(1) / r[2];
-      const R u = (r[0] * inz + fov_half) * inv_dth - R(0.5);
-      const R v = (r[1] * inz + fov_half) * inv_dth - R(0.5);
-      if (!isfinite(u) || !isfinite(v) || !isfinite(chic)) {
-        atomicOr(A.flag, 1);
-        continue;
-      }
-      if (u < R(-1) || v < R(-1) || u >= (R)A.npix || v >= (R)A.npix) continue;
-      const R fu0 = floor(u), fv0 = floor(v);
-      const int iu = (int)fu0, iv = (int)fv0;
-      const R fu = u - fu0, fv = v - fv0;
-      // Born weight in the path's precision, map accumulation in FP64
-      const R inva = interp<R>(A.tab_inva, A.tab_n, (R)A.tab_hinv, chic);
-      const R cw[4] = {(R(1) - fu) * (R(1) - fv), fu * (R(1) - fv), (R(1) - fu) * fv, fu * fv};
-      const R wk = (R)A.wpref * inva / chic;
-      for (int s = 0; s < A.nzs; ++s) {
-        const R cs_ = (R)A.chi_s[s];
-        if (!(chic < cs_)) continue;
-        const R w = wk * (cs_ - chic) / cs_;
-        const int off = s * A.npix * A.npix;
+          for (int d = 0; d < 3; ++d) q[d] += pr[d] * dt;
+        }
+        if (A.S0) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const int jx = iu + (k & 1), jy = iv + (k >> 1);
-          if (jx >= 0 && jx < A.npix && jy >= 0 && jy < A.npix) {
-            const int pix = off + jy * A.npix + jx;
-            if (A.lam) dot += (R)A.lam[pix] * w * cw[k];
-            else atomicAdd(A.maps + pix, (double)(w * cw[k]));
+          for (int d = 0; d < 3; ++d) q[d] += sr[d] * cell_len;
+        }
+        if (!(q[2] > R(0))) continue;
+        const R chic = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        const R inz = R(1) / q[2];
+        const R u = (q[0] * inz + fov_half) * inv_dth - R(0.5);
+        const R v = (q[1] * inz + fov_half) * inv_dth - R(0.5);
+        if (!isfinite(u) || !isfinite(v) || !isfinite(chic)) {
+          atomicOr(A.flag, 1);
+          continue;
+        }
+        if (u < R(-1) || v < R(-1) || u >= (R)A.npix || v >= (R)A.npix) continue;
+        const R fu0 = floor(u), fv0 = floor(v);
+        const int iu = (int)fu0, iv = (int)fv0;
+        const R fu = u - fu0, fv = v - fv0;
+        // Born weight in the path's precision, map accumulation in FP64
+        const R inva = interp<R>(V.tab_inva, A.tab_n, (R)A.tab_hinv, chic);
+        const R cw[4] = {(R(1) - fu) * (R(1) - fv), fu * (R(1) - fv), (R(1) - fu) * fv, fu * fv};
+        const R wk = (R)V.wpref * inva / chic;
+        for (int s = 0; s < A.nzs; ++s) {
+          const R cs_ = (R)V.chi_s[s];
+          if (!(chic < cs_)) continue;
+          const R w = wk * (cs_ - chic) / cs_;
+          const int off = s * A.npix * A.npix;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const int jx = iu + (k & 1), jy = iv + (k >> 1);
+            if (jx >= 0 && jx < A.npix && jy >= 0 && jy < A.npix) {
+              const int pix = off + jy * A.npix + jx;
+              if (A.lam) dot[vi] += (R)A.lam[pix] * w * cw[k];
+              else atomicAdd(A.maps + pix, (double)(w * cw[k]));
+            }
           }
         }
       }
     }
   }
-  if (A.lam) block_sum((double)dot, A.acc);
+  if (A.lam) {
+#pragma unroll
+    for (int vi = 0; vi < NV; ++vi) {
+      if (vi) __syncthreads();  // block_sum's shared scratch is reused
+      block_sum((double)dot[vi], A.var[vi].acc);
+    }
+  }
 }
 
 __global__ void k_kappa_finalize(const double* __restrict__ maps, double* __restrict__ out, long long npix2, int nzs,
@@ -211,25 +235,31 @@ cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
   // particle state read once (+ three PGD meshes gathered)
   ProfScope ps(&c->prof, KK_LENS, c->stream,
                c->np * (4.0 + 6.0 * sizeof(R)) + (use_pgd ? 3.0 * c->mesh_elems * sizeof(R) : 0.0));
-  k_lens<R><<<(int)blocks, 256, 0, c->stream>>>(A);
+  k_lens<R, 1><<<(int)blocks, 256, 0, c->stream>>>(A);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_lens_dot(pm_ctx* c, const LensShell& sh, int use_pgd, const double* lam, int tab_d1,
-                            int tab_inva, const double* chi_s, double wpref, double* acc) {
+cudaError_t launch_lens_dot2(pm_ctx* c, const LensShell& sel, int use_pgd, const double* lam, const LensDotVar& a,
+                             const LensDotVar& b) {
   LensArgs<R> A;
-  fill_lens_args<R>(c, sh, use_pgd, A);
-  A.tab_d1 = chi_table<R>(c, tab_d1);
-  A.tab_inva = chi_table<R>(c, tab_inva);
-  for (int s = 0; s < PM_MAX_ZS; ++s) A.chi_s[s] = s < c->cfg.n_zs ? chi_s[s] : 0.0;
-  A.wpref = wpref;
+  fill_lens_args<R>(c, sel, use_pgd, A);
+  const LensDotVar* in[2] = {&a, &b};
+  for (int v = 0; v < 2; ++v) {
+    LensVar<R>& V = A.var[v];
+    V.tab_d1 = chi_table<R>(c, in[v]->tab_d1);
+    V.tab_inva = chi_table<R>(c, in[v]->tab_inva);
+    for (int s = 0; s < PM_MAX_ZS; ++s) V.chi_s[s] = s < c->cfg.n_zs ? in[v]->chi_s[s] : 0.0;
+    V.wpref = in[v]->wpref;
+    V.d1_next = in[v]->d1_next;
+    V.inv_gp_half = 1.0 / in[v]->gp_half;
+    V.acc = in[v]->acc;
+  }
   A.lam = lam;
-  A.acc = acc;
   long long blocks = (c->np + 255) / 256;
   if (blocks > 152LL * 8) blocks = 152LL * 8;
   ProfScope ps(&c->prof, KK_ADJ_LENS, c->stream, c->np * (4.0 + 6.0 * sizeof(R)));
-  k_lens<R><<<(int)blocks, 256, 0, c->stream>>>(A);
+  k_lens<R, 2><<<(int)blocks, 256, 0, c->stream>>>(A);
   return cudaGetLastError();
 }
 
@@ -260,20 +290,22 @@ static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs
   A.margin = std::max(0.1 * c->cfg.box, 10.0);
   A.npix = c->cfg.map_npix;
   A.nzs = c->cfg.n_zs;
-  for (int s = 0; s < PM_MAX_ZS; ++s) A.chi_s[s] = s < c->cfg.n_zs ? c->chi_s[s] : 0.0;
+  LensVar<R>& V = A.var[0];
+  for (int s = 0; s < PM_MAX_ZS; ++s) V.chi_s[s] = s < c->cfg.n_zs ? c->chi_s[s] : 0.0;
   const double vp = std::pow(c->cfg.box / c->nc, 3.0);
-  A.wpref = 1.5 * c->cfg.omega_m / (kCoverH0 * kCoverH0) * vp / (dth * dth);
-  A.d1_next = sh.d1_next;
-  A.inv_gp_half = 1.0 / sh.gp_half;
+  V.wpref = 1.5 * c->cfg.omega_m / (kCoverH0 * kCoverH0) * vp / (dth * dth);
+  V.d1_next = sh.d1_next;
+  V.inv_gp_half = 1.0 / sh.gp_half;
+  V.tab_d1 = chi_table<R>(c, T_D1);
+  V.tab_inva = chi_table<R>(c, T_INVA);
+  V.acc = nullptr;
+  A.var[1] = V;
   A.sub = c->cfg.sub_evolution;
   A.tab_hinv = 1.0 / c->chi_tab_h;
   A.tab_n = kChiTab;
-  A.tab_d1 = chi_table<R>(c, T_D1);
-  A.tab_inva = chi_table<R>(c, T_INVA);
   A.maps = reinterpret_cast<double*>(c->ws + c->L.maps);
   A.flag = flags_ptr(c);
   A.lam = nullptr;
-  A.acc = nullptr;
   A.nrep = sh.nrep;
   for (int q = 0; q < sh.nrep; ++q) A.rep[q] = sh.rep[q];
 }
@@ -292,9 +324,9 @@ cudaError_t launch_kappa_finalize(pm_ctx* c, double* out) {
 
 template cudaError_t launch_lens<float>(pm_ctx*, const LensShell&, int);
 template cudaError_t launch_lens<double>(pm_ctx*, const LensShell&, int);
-template cudaError_t launch_lens_dot<float>(pm_ctx*, const LensShell&, int, const double*, int, int,
-                                            const double*, double, double*);
-template cudaError_t launch_lens_dot<double>(pm_ctx*, const LensShell&, int, const double*, int, int,
-                                             const double*, double, double*);
+template cudaError_t launch_lens_dot2<float>(pm_ctx*, const LensShell&, int, const double*, const LensDotVar&,
+                                             const LensDotVar&);
+template cudaError_t launch_lens_dot2<double>(pm_ctx*, const LensShell&, int, const double*, const LensDotVar&,
+                                              const LensDotVar&);
 
 }  // namespace pmlens
