@@ -43,6 +43,7 @@ struct Launch {
     cudaFuncSetAttribute(k_fft_cols<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols());
     cudaFuncSetAttribute(k_fft_cols<R, N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols());
     cudaFuncSetAttribute(k_zpass_op<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z());
+    cudaFuncSetAttribute(k_zpass_op_tma<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, ZTma<R, N>::SMEM);
     cudaFuncSetAttribute(k_zpass_combine<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_z());
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
@@ -113,11 +114,38 @@ struct Launch {
     else k_fft_cols<R, N, false><<<g, ColTile<R, N>::THREADS, smem_cols(), s>>>(d, P, (long long)N * P, N / 2 + 1);
     return cudaSuccess;
   }
-  static void zop(const C* in, const OutPtrs& o, int nout, int P, const SpecParams& sp, cudaStream_t s,
-                  Prof* pf, int kind) {
+  // fused z pass.  Force operators with an error word: the TMA pipeline, writing G and F_z
+  // (and G_p, S_z) -- the x,y components come from the dual y pass; else the tile kernel.
+  static cudaError_t zop(const C* in, const OutPtrs& o, int nout, int P, const SpecParams& sp, cudaStream_t s,
+                         Prof* pf, int kind) {
+    const bool force = sp.op == OP_FORCE || sp.op == OP_FORCE_PGD;
+    if (force && sp.err && (nout == 3 || nout == 6)) {
+      using ZT = ZTma<R, N>;
+      const int npass = nout == 6 ? 4 : 2;
+      ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_Z_OP, s, (1 + npass) * CB);
+      CUtensorMap in_map;
+      ZOutMaps om;
+      const int oi[4] = {0, 2, 3, 5};
+      bool ok = make_cols_map(&in_map, const_cast<C*>(in), N, P, ZT::W, ZT::BOXR, true, sizeof(R) == 8);
+      for (int q = 0; q < 4 && ok; ++q)
+        ok = make_cols_map(&om.m[q], o.p[q < npass ? oi[q] : 0], N, P, ZT::W, ZT::BOXR, true, sizeof(R) == 8);
+      if (!ok) return cudaErrorInvalidValue;
+      const int ntx = (N / 2 + 1 + ZT::W - 1) / ZT::W, tiles = ntx * N;
+      static const int slots = [] {
+        int per_sm = 0, dev = 0, nsm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zpass_op_tma<R, N>, ZT::THREADS, ZT::SMEM);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        return std::max(per_sm, 1) * std::max(nsm, 1);
+      }();
+      k_zpass_op_tma<R, N><<<std::min(tiles, slots), ZT::THREADS, ZT::SMEM, s>>>(in_map, om, ntx, tiles, npass, sp,
+                                                                                 sp.err);
+      return cudaSuccess;
+    }
     ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_Z_OP, s, (1 + nout) * CB);
     dim3 g((N / 2 + 1 + ZTile<R, N>::W - 1) / ZTile<R, N>::W, N);
     k_zpass_op<R, N><<<g, ZTile<R, N>::THREADS, smem_z(), s>>>(in, o, nout, P, sp);
+    return cudaSuccess;
   }
 
   static cudaError_t transpose(R* const* real_in, int nin, int first, void* const* ubufs, void* cbuf, R* real_out,
@@ -161,7 +189,7 @@ struct Launch {
     if (e) return e;
     OutPtrs o;
     for (int i = 0; i < 9; ++i) o.p[i] = i < nout ? ubufs[i] : nullptr;
-    zop(c, o, nout, P, sp, s, pf, kind);
+    if ((e = zop(c, o, nout, P, sp, s, pf, kind))) return e;
     const bool force = sp.op == OP_FORCE || sp.op == OP_FORCE_PGD;
     if (force && sp.err && (nout == 3 || nout == 6)) {
       // the z pass left G (x,y group) and the z component of each group of three

@@ -207,6 +207,135 @@ k_fft_cols_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ 
   if (leader) bulk_wait0();
 }
 
+// ------------------------------------------------------------- force z pass
+// Persistent, TMA-pipelined z pass of a force evaluation (OP_FORCE /
+// OP_FORCE_PGD): per (y plane, kx tile) column tile, forward z FFT, scale by
+// g = (3/2) Om / k^2, inverse for the x,y group (G) and for i k_z g A (F_z);
+// with PGD, rescale by the filter ratio and two more inverses (G_p, S_z).
+// The next tile's input arrives by TMA while this one is transformed; each
+// pass's result leaves by TMA store.  Shared memory: twiddles, two input
+// tiles (the current one is transformed in place), one work tile.
+template <typename R, int N> struct ZTma {
+  static constexpr int W = ZTile<R, N>::W, CP = ZTile<R, N>::CP, THREADS = ZTile<R, N>::THREADS;
+  static constexpr int BOXR = N < 256 ? N : 256;
+  static constexpr int NBOX = N / BOXR;
+  static constexpr int TILE_BYTES = N * W * 2 * (int)sizeof(R);
+  static constexpr int TW_BYTES = (N * 2 * (int)sizeof(R) + 1023) / 1024 * 1024;
+  static constexpr int SMEM = TW_BYTES + 3 * TILE_BYTES + 64;
+  static_assert((2 * W * (int)sizeof(R)) % 16 == 0, "TMA inner box extent must be a 16-byte multiple");
+  static_assert(TILE_BYTES % 1024 == 0, "tile buffers stay 1024-byte aligned");
+};
+
+struct ZOutMaps { CUtensorMap m[4]; };  // G, F_z, G_p, S_z
+
+template <typename R, int N>
+__global__ void __launch_bounds__(ZTma<R, N>::THREADS, 2)
+k_zpass_op_tma(const __grid_constant__ CUtensorMap in_map, const __grid_constant__ ZOutMaps outs, int ntx, int ntiles,
+               int npass, SpecParams sp, int* __restrict__ err) {
+  using C = typename CT<R>::T;
+  using ZT = ZTma<R, N>;
+  constexpr int W = ZT::W, CP = ZT::CP, THR = ZT::THREADS;
+  constexpr int EPT = N * W / THR;
+  extern __shared__ __align__(1024) unsigned char smem_zt[];
+  C* tw = reinterpret_cast<C*>(smem_zt);
+  auto inbuf = [&](int b) { return reinterpret_cast<C*>(smem_zt + ZT::TW_BYTES + b * ZT::TILE_BYTES); };
+  C* B = reinterpret_cast<C*>(smem_zt + ZT::TW_BYTES + 2 * ZT::TILE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_zt + ZT::TW_BYTES + 3 * ZT::TILE_BYTES);
+  int* ok_word = reinterpret_cast<int*>(bars + 2);
+  const uint32_t bar0 = smem_u32(bars);
+  auto bar = [&](int b) { return bar0 + 8u * (uint32_t)b; };
+  const bool leader = threadIdx.x == 0;
+  if (smem_u32(inbuf(0)) & 127u) {
+    if (leader) atomicOr(err, PM_FLAG_TIMEOUT);
+    return;
+  }
+  auto issue_load = [&](int ti, int b) {
+    const int plane = ti / ntx, kx0 = (ti - plane * ntx) * W;
+    mbar_expect_tx(bar(b), ZT::TILE_BYTES);
+#pragma unroll
+    for (int q = 0; q < ZT::NBOX; ++q)
+      tma_load_3d(smem_u32(inbuf(b)) + q * ZT::BOXR * W * (int)sizeof(C), &in_map, 2 * kx0, plane, q * ZT::BOXR,
+                  bar(b));
+  };
+  auto store = [&](const CUtensorMap* m, int ti, const C* src) {
+    const int plane = ti / ntx, kx0 = (ti - plane * ntx) * W;
+#pragma unroll
+    for (int q = 0; q < ZT::NBOX; ++q)
+      tma_store_3d(m, 2 * kx0, plane, q * ZT::BOXR, smem_u32(src) + q * ZT::BOXR * W * (int)sizeof(C));
+    bulk_commit();
+  };
+  if (leader) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&in_map)) : "memory");
+    mbar_init(bar(0), 1);
+    mbar_init(bar(1), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  make_twiddles<C, N>(tw);
+  __syncthreads();
+  if (leader && blockIdx.x < ntiles) issue_load(blockIdx.x, 0);
+
+  const int col = CP * (threadIdx.x % (W / CP)), t = threadIdx.x / (W / CP);
+  const R kf = (R)sp.kf;
+  constexpr int h = N / 2;
+  const R pratio = (R)(sp.pgd_scale / sp.scale);
+  int it = 0;
+  for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x, ++it) {
+    const int b = it & 1, next = ti + gridDim.x;
+    if (leader) {
+      bulk_wait_read0();  // stores of the previous tile have read their tiles
+      if (next < ntiles) issue_load(next, b ^ 1);
+    }
+    if (leader) *ok_word = mbar_wait(bar(b), (it >> 1) & 1) ? 1 : 0;
+    __syncthreads();
+    if (!*ok_word) {
+      if (leader) {
+        atomicOr(err, PM_FLAG_TIMEOUT);
+        if (next < ntiles) mbar_wait(bar(b ^ 1), ((it + 1) >> 1) & 1);
+      }
+      break;
+    }
+    mbar_wait(bar(b), (it >> 1) & 1);
+    C* A = inbuf(b);
+    const int iy = ti / ntx, kx0 = (ti - iy * ntx) * W;
+    const int fy = iy <= h ? iy : iy - N;
+    fft_column<C, N, false, W, 1, CP>(A, col, t, tw);
+    for (int pass = 0; pass < npass; ++pass) {
+      const bool zc = pass & 1;
+      const bool last = pass == npass - 1;
+      C* T = last ? A : B;
+      if (!last) {
+        // B is the previous pass's store source: wait until the copy engine has read it
+        if (leader) bulk_wait_read0();
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const int e = threadIdx.x + q * THR;
+        const int row = e / W, c = e - row * W, ix = kx0 + c;
+        C a = A[e];
+        if (!zc) {
+          const int fx = ix <= h ? ix : ix - N, fz = row <= h ? row : row - N;
+          const R k2 = kf * kf * (R)(fx * fx + fy * fy + fz * fz);
+          const R inv = k2 > R(0) ? R(1) / k2 : R(0);
+          const R f = pass == 0 ? (R)sp.scale * inv : (k2 > R(0) ? pratio * pgd_filter<R>(sp, k2, inv) : R(0));
+          a = C{f * a.x, f * a.y};
+          A[e] = a;
+          T[e] = a;
+        } else {
+          const R oz = row == h ? R(0) : kf * (R)(row <= h ? row : row - N);
+          T[e] = C{-oz * a.y, oz * a.x};  // i k_z a
+        }
+      }
+      __syncthreads();
+      fft_column<C, N, true, W, 1, CP>(T, col, t, tw);  // ends with __syncthreads
+      fence_proxy_async();
+      __syncthreads();
+      if (leader) store(&outs.m[pass], ti, T);
+    }
+  }
+  if (leader) bulk_wait0();
+}
+
 // Host side: rank-3 tensor map over a half-spectrum buffer for the column pass
 // of axis `zaxis` (false: y rows).  Returns false if the driver rejects it.
 bool make_cols_map(CUtensorMap* map, void* base, int n, int P, int w, int boxr, bool zaxis, bool dbl);
