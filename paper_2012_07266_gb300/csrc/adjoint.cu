@@ -19,6 +19,7 @@
 
 #include "adjoint.h"
 #include "cic.cuh"
+#include "lens_cull.cuh"
 
 namespace pmlens {
 
@@ -226,8 +227,12 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
   const R cell_len = (R)A.cell_len, lo2 = (R)A.chi_lo2, hi2 = (R)A.chi_hi2;
   const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
   const R tan_half = (R)A.tan_half, margin = (R)A.margin;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.np;
-       j += (long long)gridDim.x * blockDim.x) {
+  // whole warps iterate together (warp-level replica culling, as in the forward)
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); j0 < A.np; j0 += stride) {
+    const bool valid = j0 + lane < A.np;
+    const long long j = valid ? j0 + lane : A.np - 1;
     int ci[3];
     unpack3(A.st.cell[j], ci);
     const R cf[3] = {A.st.fx[j], A.st.fy[j], A.st.fz[j]};
@@ -235,7 +240,14 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
     R cs[3] = {R(0), R(0), R(0)};
     bool have_s = false;
     R gx[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
+    const WarpBox box =
+        warp_box(valid, (float)ci[0] + (float)cf[0], (float)ci[1] + (float)cf[1], (float)ci[2] + (float)cf[2]);
+    unsigned live = 0u;
     for (int q = 0; q < A.nrep; ++q) {
+      if ((q & 31) == 0)  // warp-uniform
+        live = cull_replicas(A.rep, A.nrep, q, box, A.M, (float)A.cell_len, (float)A.chi_lo2, (float)A.chi_hi2,
+                             (float)A.tan_half, (float)A.margin) & (valid ? ~0u : 0u);
+      if (!(live >> (q & 31) & 1u)) continue;
       const Replica rp = A.rep[q];
       R r[3];
 #pragma unroll
@@ -352,6 +364,7 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
         }
       }
     }
+    if (!valid) continue;
     A.lx[j] += gx[0];
     A.lx[j + A.np] += gx[1];
     A.lx[j + 2 * A.np] += gx[2];

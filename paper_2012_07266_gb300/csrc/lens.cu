@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "adjoint.h"
+#include "lens_cull.cuh"
 
 namespace pmlens {
 
@@ -106,8 +107,12 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
   R dot[NV];
 #pragma unroll
   for (int vi = 0; vi < NV; ++vi) dot[vi] = R(0);
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < A.np;
-       j += (long long)gridDim.x * blockDim.x) {
+  // whole warps iterate together (warp-level replica culling); lanes past the end add nothing
+  const int lane = threadIdx.x & 31;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long j0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); j0 < A.np; j0 += stride) {
+    const bool valid = j0 + lane < A.np;
+    const long long j = valid ? j0 + lane : A.np - 1;
     const uint32_t c = A.cell[j];
     // per-axis particle data in registers; a replica's axis permutation picks
     // among them with selects (a runtime-indexed array would live in local memory)
@@ -116,7 +121,13 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
     const R cp0 = A.px[j], cp1 = A.py[j], cp2 = A.pz[j];
     R cs0 = R(0), cs1 = R(0), cs2 = R(0);
     bool have_s = false;  // PGD displacement gathered only for particles that may land on the map
+    const WarpBox box = warp_box(valid, (float)ci0 + (float)cf0, (float)ci1 + (float)cf1, (float)ci2 + (float)cf2);
+    unsigned live = 0u;  // replicas q..q+31 any particle of the warp may reach
     for (int q = 0; q < A.nrep; ++q) {
+      if ((q & 31) == 0)  // warp-uniform
+        live = cull_replicas(A.rep, A.nrep, q, box, A.M, (float)A.cell_len, (float)A.chi_lo2, (float)A.chi_hi2,
+                             (float)A.tan_half, (float)A.margin) & (valid ? ~0u : 0u);
+      if (!(live >> (q & 31) & 1u)) continue;
       const Replica rp = A.rep[q];
       R r[3], pr[3], sr[3];
 #pragma unroll

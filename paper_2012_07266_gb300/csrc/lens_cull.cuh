@@ -1,0 +1,97 @@
+// Warp-level replica culling for the lightcone projection and its transpose.
+//
+// The particle state is kept sorted by coarse spatial bucket, so the 32
+// consecutive particles of a warp occupy a small box of the simulation volume.
+// Lane q tests that box, mapped through replica q's rotation / flip / periodic
+// shift / offset, against the shell's distance range, the line-of-sight
+// half-space and the field of view widened by the displacement margin; a
+// ballot gives the replicas any particle of the warp can reach.  The test is
+// conservative (the box is widened by a small slack against rounding, and a box
+// that straddles the periodic boundary after the transform becomes the whole
+// axis), so culled (particle, replica) pairs are exactly pairs the per-particle
+// tests would reject: the projection is unchanged, only the work shrinks.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pm_internal.h"
+
+namespace pmlens {
+namespace {
+
+// Positions in cells (original frame) of the warp's valid lanes lie in
+// [lo[a], hi[a]] per axis a.
+struct WarpBox {
+  float lo[3], hi[3];
+};
+
+__device__ __forceinline__ WarpBox warp_box(bool valid, float p0, float p1, float p2) {
+  WarpBox b;
+  const float inf = __int_as_float(0x7f800000);
+  b.lo[0] = valid ? p0 : inf; b.hi[0] = valid ? p0 : -inf;
+  b.lo[1] = valid ? p1 : inf; b.hi[1] = valid ? p1 : -inf;
+  b.lo[2] = valid ? p2 : inf; b.hi[2] = valid ? p2 : -inf;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      b.lo[a] = fminf(b.lo[a], __shfl_xor_sync(0xffffffffu, b.lo[a], o));
+      b.hi[a] = fmaxf(b.hi[a], __shfl_xor_sync(0xffffffffu, b.hi[a], o));
+    }
+  }
+  return b;
+}
+
+// false only if no position in the box can pass the shell, z > 0 and field-of-view
+// tests of the per-particle code under replica rp
+__device__ __forceinline__ bool replica_may_hit(const Replica& rp, const WarpBox& b, int M, float cell_len,
+                                                float lo2, float hi2, float tan_half, float margin) {
+  const float slack = 0.01f;  // cells: covers FP32 rounding of the per-particle positions
+  const float Mf = (float)M;
+  float bl[3], bh[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int ax = rp.perm[d];
+    float a = ax == 0 ? b.lo[0] : (ax == 1 ? b.lo[1] : b.lo[2]);
+    float h = ax == 0 ? b.hi[0] : (ax == 1 ? b.hi[1] : b.hi[2]);
+    bool full = !(a <= h);  // empty box (no valid lane): keep it simple, test the whole axis
+    if (rp.flip >> d & 1) {
+      // p -> M - p for p > 0, and 0 -> 0
+      if (a <= 0.f) full = true;
+      else { const float na = Mf - h, nh = Mf - a; a = na; h = nh; }
+    }
+    a += (float)rp.shift[d];
+    h += (float)rp.shift[d];
+    if (a >= Mf) { a -= Mf; h -= Mf; }
+    if (h >= Mf) full = true;  // straddles the periodic boundary
+    if (full) { a = 0.f; h = Mf; }
+    const float off = (float)rp.n[d] * Mf;
+    bl[d] = (a + off - slack) * cell_len;
+    bh[d] = (h + off + slack) * cell_len;
+  }
+  float dmin2 = 0.f, dmax2 = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float nearest = bl[d] > 0.f ? bl[d] : (bh[d] < 0.f ? -bh[d] : 0.f);
+    const float far = fmaxf(fabsf(bl[d]), fabsf(bh[d]));
+    dmin2 += nearest * nearest;
+    dmax2 += far * far;
+  }
+  if (dmax2 <= lo2 || dmin2 > hi2) return false;
+  if (bh[2] <= 0.f) return false;
+  const float lim = bh[2] * tan_half + margin;
+  const float nx = bl[0] > 0.f ? bl[0] : (bh[0] < 0.f ? -bh[0] : 0.f);
+  const float ny = bl[1] > 0.f ? bl[1] : (bh[1] < 0.f ? -bh[1] : 0.f);
+  return nx <= lim && ny <= lim;
+}
+
+// Bit i of the result: replica base + i may be hit by the warp (nrep - base <= 32 used).
+__device__ __forceinline__ unsigned cull_replicas(const Replica* rep, int nrep, int base, const WarpBox& b, int M,
+                                                  float cell_len, float lo2, float hi2, float tan_half, float margin) {
+  const int q = base + (threadIdx.x & 31);
+  const bool hit = q < nrep && replica_may_hit(rep[q], b, M, cell_len, lo2, hi2, tan_half, margin);
+  return __ballot_sync(0xffffffffu, hit);
+}
+
+}  // namespace
+}  // namespace pmlens
