@@ -242,12 +242,8 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
     R gx[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
     const WarpBox box =
         warp_box(valid, (float)ci[0] + (float)cf[0], (float)ci[1] + (float)cf[1], (float)ci[2] + (float)cf[2]);
-    unsigned live = 0u;
-    for (int q = 0; q < A.nrep; ++q) {
-      if ((q & 31) == 0)  // warp-uniform
-        live = cull_replicas(A.rep, A.nrep, q, box, A.M, (float)A.cell_len, (float)A.chi_lo2, (float)A.chi_hi2,
-                             (float)A.tan_half, (float)A.margin) & (valid ? ~0u : 0u);
-      if (!(live >> (q & 31) & 1u)) continue;
+    // one replica of this particle (the per-particle tests below decide exactly)
+    auto project = [&](int q) {
       const Replica rp = A.rep[q];
       R r[3];
 #pragma unroll
@@ -264,9 +260,9 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
         r[d] = ((R)(i + rp.n[d] * A.M) + f) * cell_len;
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) continue;
+      if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) return;
       const R lim = r[2] * tan_half + margin;
-      if (fabs(r[0]) > lim || fabs(r[1]) > lim) continue;
+      if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
       if (A.S0 && !have_s) {
         const R* Sm[3] = {A.S0, A.S1, A.S2};
         long long o[8];
@@ -303,13 +299,13 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
 #pragma unroll
         for (int d = 0; d < 3; ++d) rc[d] += sr[d] * cell_len;
       }
-      if (!(rc[2] > R(0))) continue;
+      if (!(rc[2] > R(0))) return;
       const R chic = sqrt(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]);
       const R inz = R(1) / rc[2];
       const R u = (rc[0] * inz + fov_half) * inv_dth - R(0.5);
       const R v = (rc[1] * inz + fov_half) * inv_dth - R(0.5);
-      if (!isfinite(u) || !isfinite(v)) continue;
-      if (u < R(-1) || v < R(-1) || u >= (R)A.npix || v >= (R)A.npix) continue;
+      if (!isfinite(u) || !isfinite(v)) return;
+      if (u < R(-1) || v < R(-1) || u >= (R)A.npix || v >= (R)A.npix) return;
       const R fu0 = floor(u), fv0 = floor(v);
       const int iu = (int)fu0, iv = (int)fv0;
       const R fu = u - fu0, fv = v - fv0;
@@ -362,6 +358,17 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
           gp[a] += hit ? vp : R(0);
           gs[a] += hit ? vs : R(0);
         }
+      }
+    };
+    for (int base = 0; base < A.nrep; base += 32) {
+      // replicas base..base+31 any particle of the warp may reach (warp-uniform ballot)
+      unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, (float)A.cell_len, (float)A.chi_lo2,
+                                    (float)A.chi_hi2, (float)A.tan_half, (float)A.margin);
+      if (!valid) live = 0u;
+      while (live) {
+        const int q = base + __ffs(live) - 1;
+        live &= live - 1u;
+        project(q);
       }
     }
     if (!valid) continue;

@@ -122,12 +122,8 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
     R cs0 = R(0), cs1 = R(0), cs2 = R(0);
     bool have_s = false;  // PGD displacement gathered only for particles that may land on the map
     const WarpBox box = warp_box(valid, (float)ci0 + (float)cf0, (float)ci1 + (float)cf1, (float)ci2 + (float)cf2);
-    unsigned live = 0u;  // replicas q..q+31 any particle of the warp may reach
-    for (int q = 0; q < A.nrep; ++q) {
-      if ((q & 31) == 0)  // warp-uniform
-        live = cull_replicas(A.rep, A.nrep, q, box, A.M, (float)A.cell_len, (float)A.chi_lo2, (float)A.chi_hi2,
-                             (float)A.tan_half, (float)A.margin) & (valid ? ~0u : 0u);
-      if (!(live >> (q & 31) & 1u)) continue;
+    // one replica of this particle (the per-particle tests below decide exactly)
+    auto project = [&](int q) {
       const Replica rp = A.rep[q];
       R r[3], pr[3], sr[3];
 #pragma unroll
@@ -148,10 +144,10 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         sr[d] = sg * pick3(ax, cs0, cs1, cs2);
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) continue;
+      if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) return;
       // outside the field of view by more than the displacement margin: no weight on the map
       const R lim = r[2] * tan_half + margin;
-      if (fabs(r[0]) > lim || fabs(r[1]) > lim) continue;
+      if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
       if (A.S0 && !have_s) {
         cs0 = gather3(A.S0, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
         cs1 = gather3(A.S1, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
@@ -210,6 +206,17 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
             }
           }
         }
+      }
+    };
+    for (int base = 0; base < A.nrep; base += 32) {
+      // replicas base..base+31 any particle of the warp may reach (warp-uniform ballot)
+      unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, (float)A.cell_len, (float)A.chi_lo2,
+                                    (float)A.chi_hi2, (float)A.tan_half, (float)A.margin);
+      if (!valid) live = 0u;
+      while (live) {
+        const int q = base + __ffs(live) - 1;
+        live &= live - 1u;
+        project(q);
       }
     }
   }
