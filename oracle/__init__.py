@@ -1,4 +1,5 @@
-"""FP64 CPU oracle of the particle-mesh lensing forward model and its adjoint.
+"""FP64 CPU oracle of the particle-mesh lensing forward model, its adjoint and
+its tangent-linear model.
 
 TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports this package:
 only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
@@ -14,6 +15,8 @@ quadrature, ODE integration, interpolation), following the paper's method:
   ``lightcone``, ``mesh``)
 * Appendix A -- comoving distance integral, Eisenstein-Hu linear power,
   finite-difference cosmology derivatives (``cosmology``, ``adjoint``)
+* Sec. 3 / Fig. 8 -- the forward-mode derivative along a noise direction
+  (``jvp``), pinned to the reverse sweep by the dot-product identity
 
 Readings of points the paper leaves open are stated in each function's
 docstring.  Parity unpinned: absolute Eisenstein-Hu transfer values (only
