@@ -82,7 +82,10 @@ typedef struct {
   uint64_t rotation_seed;  /* seed of the per-replica rotation hash                  */
   int32_t rotate;          /* 1: rotate/shift each box replica                       */
   int32_t precision;       /* PM_FP32 (fast path) or PM_FP64 (plain comparator)      */
-  int32_t ckpt_every;      /* adjoint checkpoint interval in steps; 0 = no adjoint   */
+  int32_t ckpt_every;      /* adjoint checkpoint interval in steps; 0 = no adjoint;
+                              >= nsteps: resident adjoint (every step kept, no
+                              recompute in the reverse sweep)                        */
+  int32_t jvp;             /* 1: keep the tangent state of pm_jvp                    */
 } pm_config;
 
 /* Device bytes the workspace of this configuration needs (its HBM footprint,
@@ -132,6 +135,19 @@ pm_status kappa_maps(pm_ctx* ctx, double* d_maps);
  * (either output pointer may be NULL).  Synchronises the stream. */
 pm_status pm_vjp(pm_ctx* ctx, const double* d_dL_dkappa, double* d_dL_dnoise,
                  double* h_dL_dparams);
+
+/* Forward-mode derivative (JVP) of the maps along a direction of the initial
+ * white noise (Sec. 3: the model is differentiable in the initial modes; the
+ * paper checks its Jacobian-vector product by changing the initial field in
+ * one pixel, Fig. 8).  Runs the whole forward model from d_noise (pm_ic, every
+ * pm_step and lens_project) with the tangent state carried alongside, and
+ * writes the maps (as kappa_maps) to d_kappa and their derivative along
+ * d_dnoise to d_dkappa.  d_noise, d_dnoise: nc^3 float64 (device, [z][y][x]);
+ * d_kappa, d_dkappa: n_zs * npix^2 float64 outputs (device, caller-owned).
+ * Requires cfg->jvp = 1 (PM_ERR_UNSUPPORTED otherwise).  The context is left
+ * as after a full forward run (a pm_vjp may follow when ckpt_every > 0).
+ * Synchronises the stream; PM_ERR_NONFINITE as kappa_maps. */
+pm_status pm_jvp(pm_ctx* ctx, const double* d_noise, const double* d_dnoise, double* d_kappa, double* d_dkappa);
 
 /* Free the context (not the caller's workspace). */
 pm_status pm_destroy(pm_ctx* ctx);

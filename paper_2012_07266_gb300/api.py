@@ -79,6 +79,17 @@ class Simulation:
             self.lens_project(i)
         return self.kappa_maps()
 
+    def jvp(self, noise: torch.Tensor, dnoise: torch.Tensor):
+        """(kappa, dkappa): a whole forward run from `noise` and the derivative of
+        the maps along the noise direction `dnoise` (needs jvp=1 in the workload)."""
+        noise = noise.to(device=self.device, dtype=torch.float64).contiguous()
+        dnoise = dnoise.to(device=self.device, dtype=torch.float64).contiguous()
+        self._noise = (noise, dnoise)  # kept alive until the stream has consumed them
+        kappa = self._f64(self.n_zs, self.npix, self.npix)
+        dkappa = self._f64(self.n_zs, self.npix, self.npix)
+        lib.call("pm_jvp", self.ctx, _ptr(noise), _ptr(dnoise), _ptr(kappa), _ptr(dkappa))
+        return kappa, dkappa
+
     def vjp(self, dL_dkappa: torch.Tensor, want_noise=True):
         g = dL_dkappa.to(device=self.device, dtype=torch.float64).contiguous()
         dn = self._f64(self.nc, self.nc, self.nc) if want_noise else None

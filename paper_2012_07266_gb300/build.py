@@ -33,6 +33,7 @@ UNITS = [
     ("static_forces.cu", "static_forces.o", []),
     ("adjoint.cu", "adjoint.o", []),
     ("sort.cu", "sort.o", []),
+    ("jvp.cu", "jvp.o", []),
 ]
 
 

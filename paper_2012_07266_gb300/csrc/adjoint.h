@@ -77,4 +77,24 @@ template <typename R>
 cudaError_t launch_lens_dot2(pm_ctx* c, const LensShell& sel, int use_pgd, const double* lam, const LensDotVar& a,
                              const LensDotVar& b);
 
+// ---------------------------------------------------------- tangent-linear (jvp.cu)
+// IC: dx, dp from the tangent displacements (lattice order)
+template <typename R>
+cudaError_t launch_tan_ic(pm_ctx* c, R* const* dpsi1, R* const* dpsi2, double d1, double d2, double g1, double g2);
+// tangent of the 2LPT source from the base (d) and tangent (dd) second derivatives
+template <typename R>
+cudaError_t launch_lpt2_source_tan(pm_ctx* c, R* const* d, R* const* dd, R* out, long long n);
+// d rho from dx at the current positions (rho zeroed by the caller)
+template <typename R>
+cudaError_t launch_tan_paint(pm_ctx* c, R* rho);
+// tangent kick + drift of step i at x_i (F at fmesh_at(c), dF at L.tan_f)
+template <typename R>
+cudaError_t launch_tan_kd(pm_ctx* c, double ckick, double cdrift);
+// tangent of a shell's map increments into L.tan_maps
+template <typename R>
+cudaError_t launch_tan_lens(pm_ctx* c, const LensShell& sh, int use_pgd);
+// re-order the tangent state after a sort of the particle state
+template <typename R>
+cudaError_t tan_permute(pm_ctx* c, const uint32_t* old_pid, const uint32_t* new_pid);
+
 }  // namespace pmlens

@@ -30,6 +30,7 @@ pm_status check_config(const pm_config* c) {
   if (c->precision != PM_FP32 && c->precision != PM_FP64) return PM_ERR_ARG;
   if (c->pgd && !(c->pgd_params[2] >= 0 && c->pgd_params[3] > 0 && c->pgd_params[4] > 0)) return PM_ERR_ARG;
   if (c->ckpt_every < 0) return PM_ERR_ARG;
+  if (c->jvp != 0 && c->jvp != 1) return PM_ERR_ARG;
   return PM_OK;
 }
 
@@ -74,11 +75,22 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
   L.state_bytes = 2 * al(np * 4) + 2 * al(3 * np * rs);  // cell | frac | mom | pid
   L.nck = 0;
   L.nic = 0;
+  size_t a = L.adj;
+  if (cfg.ckpt_every > 0 || cfg.jvp) {
+    // derivative tables: dD1/dchi, d(1/a)/dchi and the Omega_m +/- h coefficient sets
+    L.tab_dd1 = a; a += al(kChiTab * 8);
+    L.tab_dinva = a; a += al(kChiTab * 8);
+    L.tab_d1p = a; a += al(kChiTab * 8);
+    L.tab_d1m = a; a += al(kChiTab * 8);
+    L.tab_invap = a; a += al(kChiTab * 8);
+    L.tab_invam = a; a += al(kChiTab * 8);
+    L.sqrtp_p = a; a += al((3 * (nc / 2) * (nc / 2) + 1) * 8);
+    L.sqrtp_m = a; a += al((3 * (nc / 2) * (nc / 2) + 1) * 8);
+  }
   if (cfg.ckpt_every > 0) {
     const int k = cfg.ckpt_every;
     L.nck = (cfg.nsteps + k - 1) / k;
     L.nic = 28;
-    size_t a = L.adj;
     L.adj_noise = a; a += al(grid);
     L.adj_ckpt = a; a += (size_t)L.nck * L.state_bytes;
     L.adj_seg = a; a += (size_t)(std::min(k, cfg.nsteps) + 1) * L.state_bytes;
@@ -91,17 +103,20 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
     L.adj_vs = a; a += al(3 * np * rs);
     L.adj_paint = a; a += 3 * al(mesh);
     L.adj_ic = a; a += (size_t)L.nic * al(grid);
-    L.tab_dd1 = a; a += al(kChiTab * 8);
-    L.tab_dinva = a; a += al(kChiTab * 8);
-    L.tab_d1p = a; a += al(kChiTab * 8);
-    L.tab_d1m = a; a += al(kChiTab * 8);
-    L.tab_invap = a; a += al(kChiTab * 8);
-    L.tab_invam = a; a += al(kChiTab * 8);
-    L.sqrtp_p = a; a += al((3 * (nc / 2) * (nc / 2) + 1) * 8);
-    L.sqrtp_m = a; a += al((3 * (nc / 2) * (nc / 2) + 1) * 8);
     L.adj_acc = a; a += al((size_t)(4 * cfg.nsteps + 64) * 8);
-    L.total = a;
   }
+  if (cfg.jvp) {
+    // tangent state along a noise direction: dx, dp (cells), a permutation buffer,
+    // dF (and dS) meshes at the current positions, the tangent maps, IC fields
+    L.tan_x = a; a += al(3 * np * rs);
+    L.tan_p = a; a += al(3 * np * rs);
+    L.tan_tmp = a; a += al(3 * np * rs);
+    L.tan_f = a; a += 3 * al(mesh);
+    L.tan_s = a; a += cfg.pgd ? 3 * al(mesh) : 0;
+    L.tan_maps = a; a += al((size_t)cfg.n_zs * cfg.map_npix * cfg.map_npix * 8);
+    L.tan_ic = a; a += 14 * al(grid);  // noise direction, 9 LPT fields, source, 3 Psi2
+  }
+  L.total = a;
 }
 
 template <typename R>
@@ -349,6 +364,29 @@ pm_status do_ic(pm_ctx* c, const double* d_noise) {
   }
   const double a0 = c->a[0];
   const Cosmo& co = c->cosmo;
+  if (c->tan_noise) {
+    // tangent initial conditions along the noise direction (pm_jvp): the same
+    // spectral operators on the direction, the 2LPT source linearised about
+    // the base second derivatives outs[3..8]
+    auto tf = [&](int q) { return rp<R>(c, c->L.tan_ic + (size_t)q * al(g * c->rsz)); };
+    if ((e = launch_convert_in<R>(c->tan_noise, tf(0), g, s, &c->prof))) return PM_ERR_CUDA;
+    R* touts[13];
+    for (int o = 0; o < 13; ++o) touts[o] = tf(1 + o);
+    if ((e = spectral_apply<R>(tf(0), c->ws + c->L.ic_cbuf, ub, touts, nout, c->nc, c->Pc, sp, s, &c->prof,
+                               KK_JVP)))
+      return PM_ERR_CUDA;
+    if (cfg.lpt_order == 2) {
+      if ((e = launch_lpt2_source_tan<R>(c, outs + 3, touts + 3, touts[9], g))) return PM_ERR_CUDA;
+      SpecParams sp2 = sp;
+      sp2.op = OP_GRAD_NEG;
+      if ((e = spectral_apply<R>(touts[9], c->ws + c->L.ic_cbuf, ub, touts + 10, 3, c->nc, c->Pc, sp2, s,
+                                 &c->prof, KK_JVP)))
+        return PM_ERR_CUDA;
+    }
+    if ((e = launch_tan_ic<R>(c, touts, psi2 ? touts + 10 : nullptr, co.D1(a0), psi2 ? co.D2(a0) : 0.0, co.gp(a0),
+                              psi2 ? co.gp2(a0) : 0.0)))
+      return PM_ERR_CUDA;
+  }
   if ((e = launch_ic_particles<R>(c, outs, psi2, co.D1(a0), psi2 ? co.D2(a0) : 0.0, co.gp(a0),
                                   psi2 ? co.gp2(a0) : 0.0)))
     return PM_ERR_CUDA;
@@ -869,6 +907,54 @@ pm_status do_density(pm_ctx* c, double* out) {
   return cuda_status(launch_convert_out<R>(rho, out, c->mesh_elems, 1.0, c->stream, &c->prof));
 }
 
+// d rho at the current positions from dx, then the force (and PGD) operator on it:
+// dF (dS) meshes into the tangent slots
+template <typename R>
+cudaError_t tan_force(pm_ctx* c, bool pgd, double alpha) {
+  R* rho = rp<R>(c, c->L.rho);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, c->stream))) return e;
+  if ((e = launch_tan_paint<R>(c, rho))) return e;
+  return force_from_rho<R>(c, pgd, alpha, pgd ? c->L.tan_s : 0, c->L.tan_f);
+}
+
+template <typename R>
+pm_status do_tan_lens(pm_ctx* c, int i) {
+  LensShell sh = make_shell(c, i, c->cosmo);
+  const std::vector<Replica> reps = shell_replicas(c, std::sqrt(sh.chi_lo2), std::sqrt(sh.chi_hi2));
+  for (size_t b = 0; b < reps.size(); b += kMaxReplicas) {
+    sh.nrep = (int)std::min<size_t>(kMaxReplicas, reps.size() - b);
+    for (int q = 0; q < sh.nrep; ++q) sh.rep[q] = reps[b + q];
+    if (launch_tan_lens<R>(c, sh, c->cfg.pgd && c->pgd_valid)) return PM_ERR_CUDA;
+  }
+  return PM_OK;
+}
+
+// forward run with the tangent state alongside (see pm_jvp)
+template <typename R>
+pm_status do_jvp(pm_ctx* c, const double* noise, const double* dnoise, double* kappa, double* dkappa) {
+  const pm_config& cfg = c->cfg;
+  const size_t map_bytes = (size_t)cfg.n_zs * cfg.map_npix * cfg.map_npix * 8;
+  if (cudaMemsetAsync(c->ws + c->L.tan_maps, 0, map_bytes, c->stream)) return PM_ERR_CUDA;
+  c->tan_noise = dnoise;
+  pm_status st = pm_ic(c, noise);  // primal IC and the tangent dx0, dp0
+  c->tan_noise = nullptr;
+  if (st) return st;
+  c->tan_on = 1;
+  if (tan_force<R>(c, false, 0.0)) return PM_ERR_CUDA;  // dF(x_0)
+  for (int i = 0; i < cfg.nsteps; ++i) {
+    if (launch_tan_kd<R>(c, c->kick[i], c->drift[i])) return PM_ERR_CUDA;  // at x_i, before the primal moves
+    if ((st = pm_step(c, i))) return st;                                   // x_{i+1}; re-sorts the tangent too
+    const bool pgd = cfg.pgd && shell_active(c, i);
+    if (tan_force<R>(c, pgd, pgd ? pgd_alpha(c, i) : 0.0)) return PM_ERR_CUDA;  // dF(x_{i+1}), dS(x_{i+1})
+    if ((st = lens_project(c, i))) return st;
+    if (shell_active(c, i) && (st = do_tan_lens<R>(c, i))) return st;
+  }
+  if (cudaMemcpyAsync(dkappa, c->ws + c->L.tan_maps, map_bytes, cudaMemcpyDeviceToDevice, c->stream))
+    return PM_ERR_CUDA;
+  return kappa_maps(c, kappa);
+}
+
 }  // namespace
 
 extern "C" {
@@ -919,7 +1005,7 @@ pm_status pm_init(pm_ctx** out, const pm_config* cfg, void* d_workspace, size_t 
   c->vjp_state_lost = 0;
   build_tables(c);
   if (upload_tables(c) != cudaSuccess) { delete c; return PM_ERR_CUDA; }
-  if (cfg->ckpt_every > 0) {
+  if (cfg->ckpt_every > 0 || cfg->jvp) {
     build_adjoint_tables(c);
     if (upload_adjoint_tables(c) != cudaSuccess) { delete c; return PM_ERR_CUDA; }
   }
@@ -965,6 +1051,13 @@ pm_status pm_step(pm_ctx* c, int32_t i) {
   if (sorted) {
     cudaError_t e = c->prec == PM_FP64 ? sort_particles<double>(c) : sort_particles<float>(c);
     if (e) return PM_ERR_CUDA;
+    if (c->tan_on) {
+      // the sort swapped the state buffers: the old order's pid is now in L.pid2
+      const uint32_t* old_pid = reinterpret_cast<const uint32_t*>(c->ws + c->L.pid2);
+      const uint32_t* new_pid = reinterpret_cast<const uint32_t*>(c->ws + c->L.pid);
+      e = c->prec == PM_FP64 ? tan_permute<double>(c, old_pid, new_pid) : tan_permute<float>(c, old_pid, new_pid);
+      if (e) return PM_ERR_CUDA;
+    }
   }
   if (adj_resident(c->cfg)) {
     // keep x_{i+1}, p_{i+1/2} in the order step i+1 uses
@@ -1007,6 +1100,15 @@ pm_status pm_vjp(pm_ctx* c, const double* d_dL_dkappa, double* d_dL_dnoise, doub
   // the reverse sweep reuses the particle arrays: the forward state is gone
   c->last_stepped = -1;
   c->vjp_state_lost = 1;
+  return st;
+}
+
+pm_status pm_jvp(pm_ctx* c, const double* d_noise, const double* d_dnoise, double* d_kappa, double* d_dkappa) {
+  if (!c || !d_noise || !d_dnoise || !d_kappa || !d_dkappa) return PM_ERR_ARG;
+  if (!c->cfg.jvp) return PM_ERR_UNSUPPORTED;
+  pm_status st = PM_DISPATCH(c, do_jvp, c, d_noise, d_dnoise, d_kappa, d_dkappa);
+  c->tan_on = 0;
+  c->tan_noise = nullptr;
   return st;
 }
 

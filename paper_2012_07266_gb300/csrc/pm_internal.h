@@ -59,7 +59,7 @@ struct LensShell {
 // kernel classes for launch counting and optional event timing
 enum KernelKind {
   KK_KDK_PAINT = 0, KK_PAINT, KK_FFT_X_FWD, KK_FFT_Y_FWD, KK_FFT_Z_FWD, KK_FFT_Z_OP, KK_FFT_Y_INV,
-  KK_FFT_X_INV, KK_LENS, KK_IC, KK_MISC, KK_ADJ, KK_ADJ_FFT, KK_ADJ_LENS, KK_COUNT
+  KK_FFT_X_INV, KK_LENS, KK_IC, KK_MISC, KK_ADJ, KK_ADJ_FFT, KK_ADJ_LENS, KK_JVP, KK_COUNT
 };
 const char* kernel_kind_name(int k);
 
@@ -105,6 +105,7 @@ struct Layout {
   // adjoint storage (ckpt_every > 0)
   size_t adj;
   size_t state_bytes;       // one particle state: cell | frac x3 | mom x3
+  size_t tan_x, tan_p, tan_tmp, tan_f, tan_s, tan_maps, tan_ic;
   size_t adj_noise, adj_ckpt, adj_seg, adj_fseg, adj_sseg, adj_lx, adj_lp, adj_v, adj_vs, adj_paint, adj_ic;
   size_t tab_dd1, tab_dinva, tab_d1p, tab_d1m, tab_invap, tab_invam, sqrtp_p, sqrtp_m, adj_acc;
   int nck, nic;             // checkpoints, IC adjoint fields
@@ -145,6 +146,8 @@ struct pm_ctx {
   size_t s_at = 0;   // workspace offset of the PGD meshes the lens kernels read (0: L.smesh)
   size_t f_at = 0;   // workspace offset of the current force meshes (0: L.fmesh)
   std::vector<char> sorted_after;  // resident adjoint: the state was re-sorted at the end of step i
+  const double* tan_noise = nullptr;  // pm_jvp: noise direction for the tangent initial conditions
+  int tan_on = 0;                     // pm_jvp: the tangent state follows the particle order
   int ic_done;
   int vjp_state_lost;  // 1: checkpoints do not describe the current run
   pmlens::Prof prof;

@@ -19,7 +19,7 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_WORKSPACE", 3: "PM_ERR_CUDA",
 
 # every symbol include/pm.h declares
 EXPORTS = ["pm_workspace_size", "pm_init", "pm_ic", "pm_step", "lens_project", "kappa_maps",
-           "pm_vjp", "pm_destroy", "pm_strerror", "pm_get_particles", "pm_set_particles",
+           "pm_vjp", "pm_jvp", "pm_destroy", "pm_strerror", "pm_get_particles", "pm_set_particles",
            "pm_get_forces", "pm_get_pgd", "pm_fft_r2c", "pm_get_density", "pm_sync_status",
            "pm_profile", "pm_profile_read", "pm_kernel_kinds", "pm_kernel_name",
            "pm_forces_static"]
@@ -36,7 +36,7 @@ class PMConfig(C.Structure):
         ("map_npix", C.c_int32), ("map_fov_deg", C.c_double),
         ("sub_evolution", C.c_int32), ("pgd", C.c_int32), ("pgd_params", C.c_double * 5),
         ("rotation_seed", C.c_uint64), ("rotate", C.c_int32), ("precision", C.c_int32),
-        ("ckpt_every", C.c_int32),
+        ("ckpt_every", C.c_int32), ("jvp", C.c_int32),
     ]
 
 
@@ -69,6 +69,7 @@ def make_config(w: dict, precision=PM_FP32) -> PMConfig:
     c.rotate = int(w.get("rotate", 1))
     c.precision = int(w.get("precision", precision))
     c.ckpt_every = int(w.get("ckpt_every", 0))
+    c.jvp = int(w.get("jvp", 0))
     return c
 
 
@@ -93,6 +94,7 @@ def load():
         "lens_project": [vp, i32],
         "kappa_maps": [vp, vp],
         "pm_vjp": [vp, vp, vp, vp],
+        "pm_jvp": [vp, vp, vp, vp, vp],
         "pm_destroy": [vp],
         "pm_get_particles": [vp, vp, vp],
         "pm_set_particles": [vp, vp, vp, i32],
