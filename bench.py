@@ -291,6 +291,15 @@ def run_gpu(a, rank, world, local_rank):
                "sample": f"one FP64 oracle kick-drift step with PM force of {w['nc']}^3 particles on the "
                          f"{w['nmesh']}^3 mesh ({dt:.1f} s), single-threaded numpy"}
     extra = {} if (a.no_extra or world > 1) else extra_legs(a, w, dev, rank)
+    # whole-step roofline against the byte model of a KDK step (paint, forward FFT,
+    # three inverse FFTs with the fused Poisson/gradient, readout + kick, drift):
+    # 9 R + 20 C + 100 N_p bytes, R = 4 M^3, C = 8 M^2 (M/2 + 1)
+    M = w["nmesh"]
+    step_bytes = 9 * 4.0 * M ** 3 + 20 * 8.0 * M * M * (M // 2 + 1) + 100.0 * npart
+    at_peak = peak * 1e9 / step_bytes * npart
+    model = {"bytes_per_step_gb": round(step_bytes / 1e9, 2), "particle_steps_per_s_at_peak": at_peak,
+             "frac": round(value / (world * at_peak), 4), "peak_gbs": peak, "peak_source": peak_src}
+    maps_per_hour = world * 3600.0 / (ms * 1e-3) * len(w["zs"])  # one map per source plane
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == PM_FP32 else "f64", "data": "synthetic",
@@ -299,7 +308,8 @@ def run_gpu(a, rank, world, local_rank):
                        "l2": "inputs larger than L2 (workspace %.1f GB)" % (sim.nbytes / 1e9),
                        "parallelism": f"replicas x{world}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
-            "cpu_baseline": cpu, "kernels": kern, **extra}
+            "cpu_baseline": cpu, "kernels": kern, "step_roofline_model": model,
+            "kappa_maps_per_hour": maps_per_hour, **extra}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
@@ -315,38 +325,52 @@ def extra_legs(a, w, dev, rank):
     out = {}
     npart, nsteps = w["nc"] ** 3, w["nsteps"]
     noise = torch.from_numpy(white_noise(w["nc"], w["noise_seed"] + rank)).to(dev)
-    # forward + reverse-mode derivative (checkpoint every 4 steps)
-    wa = dict(w, ckpt_every=4)
+    # forward + reverse-mode derivative: resident (every step's state and meshes kept in HBM,
+    # no recompute) and checkpointed every 4 steps (one recompute of each segment)
     stream = torch.cuda.Stream(dev)
-    sim = Simulation(device=dev, stream=stream, precision=PM_FP32, **wa)
-    lam = None
 
-    def fwd_adj():
-        nonlocal lam
+    def time_fwd_adj(ckpt):
+        sim = Simulation(device=dev, stream=stream, precision=PM_FP32, **dict(w, ckpt_every=ckpt))
         k = sim.run(noise)
-        lam = k if lam is None else lam
+        lam = k.clone()
         sim.vjp(lam)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        reps = 2
+        t_f = t_fa = 0.0
+        for _ in range(reps):
+            e0.record(stream)
+            k = sim.run(noise)
+            e1.record(stream)
+            sim.vjp(lam)
+            e2.record(stream)
+            e2.synchronize()
+            t_f += e0.elapsed_time(e1)
+            t_fa += e0.elapsed_time(e2)
+        t_f, t_fa = t_f / reps, t_fa / reps
+        gb = sim.nbytes / 1e9
+        del sim
+        torch.cuda.empty_cache()
+        return {"value": npart * nsteps / (t_fa * 1e-3), "unit": UNIT, "ms_per_step": t_fa, "forward_ms": t_f,
+                "adjoint_over_forward": (t_fa - t_f) / t_f, "checkpoint_every": ckpt, "workspace_gb": gb}, k
 
-    fwd_adj()
-    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-    reps = 2
-    t_f = t_fa = 0.0
-    for _ in range(reps):
-        e0.record(stream)
-        k = sim.run(noise)
-        e1.record(stream)
-        sim.vjp(lam)
-        e2.record(stream)
-        e2.synchronize()
-        t_f += e0.elapsed_time(e1)
-        t_fa += e0.elapsed_time(e2)
-    t_f, t_fa = t_f / reps, t_fa / reps
-    out["fwd_adjoint"] = {"value": npart * nsteps / (t_fa * 1e-3), "unit": UNIT, "ms_per_step": t_fa,
-                          "forward_ms": t_f, "adjoint_over_forward": (t_fa - t_f) / t_f,
-                          "checkpoint_every": 4, "workspace_gb": sim.nbytes / 1e9}
-    kappa32 = k.clone()
+    out["fwd_adjoint"], k = time_fwd_adj(nsteps)
+    out["fwd_adjoint_ckpt4"], _ = time_fwd_adj(4)
+    # forward-mode derivative along a noise direction (one whole run with the tangent)
+    sim = Simulation(device=dev, stream=stream, precision=PM_FP32, **dict(w, jvp=1))
+    d = torch.from_numpy(white_noise(w["nc"], w["noise_seed"] + 1000)).to(dev)
+    sim.jvp(noise, d)
+    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+    e0.record(stream)
+    for _ in range(2):
+        sim.jvp(noise, d)
+    e1.record(stream)
+    e1.synchronize()
+    t_j = e0.elapsed_time(e1) / 2
+    out["fwd_jvp"] = {"value": npart * nsteps / (t_j * 1e-3), "unit": UNIT, "ms_per_step": t_j,
+                      "jvp_over_forward": t_j / out["fwd_adjoint"]["forward_ms"], "workspace_gb": sim.nbytes / 1e9}
     del sim
     torch.cuda.empty_cache()
+    kappa32 = k.clone()
     # plain FP64 path, one simulation at a time
     sim = Simulation(device=dev, stream=stream, precision=PM_FP64, **w)
     sim.run(noise)
@@ -357,7 +381,7 @@ def extra_legs(a, w, dev, rank):
     t64 = e0.elapsed_time(e1)
     err = float((kappa32 - k64).norm() / k64.norm())
     out["plain_fp64"] = {"value": npart * nsteps / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64,
-                         "fp32_speedup": t64 / t_f, "kappa_rel_l2_fp32_vs_fp64": err}
+                         "fp32_speedup": t64 / out["fwd_adjoint"]["forward_ms"], "kappa_rel_l2_fp32_vs_fp64": err}
     del sim
     torch.cuda.empty_cache()
     # serving mix: Poisson arrivals at 20/s, meshes 64/128/192 (nc = mesh/2)
