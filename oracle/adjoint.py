@@ -129,10 +129,16 @@ def project_vjp(geom: LensGeometry, i, x, p, S, lam):
         fu, fv = u - iu, v - iv
         g_rc = np.zeros_like(rc)
         for s, cs in enumerate(geom.chi_s):
-            inside = (chic < cs) & ok
-            f = 1.0 / chic - 1.0 / cs                 # (chi_s - chi)/(chi_s chi)
-            w = np.where(inside, K * f * inva, 0.0)
-            dw = np.where(inside, K * (-inva / chic ** 2 + f * dinva), 0.0)
+            if geom.nz[s] is None:
+                inside = (chic < cs) & ok
+                f = 1.0 / chic - 1.0 / cs                 # (chi_s - chi)/(chi_s chi)
+                w = np.where(inside, K * f * inva, 0.0)
+                dw = np.where(inside, K * (-inva / chic ** 2 + f * dinva), 0.0)
+            else:
+                # w = K q(chi) / (chi a): d/dchi = K [(q' chi - q) / chi^2 / a + q / chi d(1/a)/dchi]
+                q, dq = geom.source_weight(s, chic)
+                w = np.where(ok, K * q / chic * inva, 0.0)
+                dw = np.where(ok, K * ((dq * chic - q) / chic ** 2 * inva + q / chic * dinva), 0.0)
             Lw = np.zeros(len(sel))
             Lu = np.zeros(len(sel))
             Lv = np.zeros(len(sel))
@@ -273,6 +279,9 @@ def vjp(sim, noise, lam, h_om=1e-4):
         gg = LensGeometry(c, stp_, geom.zs, geom.npix, np.rad2deg(geom.fov), L, nc, M,
                           rotate=geom.rotate, seed=geom.seed, sub_evolution=geom.sub_evolution)
         gg.chi_a = geom.chi_a      # selection at the central cosmology
+        for s, spec in enumerate(geom.nz):
+            if spec is not None:   # the same n(z); its distances in the perturbed cosmology
+                gg.set_source_nz(s, spec[0], spec[1])
         return gg
 
     gp_, gm_ = geom_for(cp, stp), geom_for(cm, stm)

@@ -160,10 +160,15 @@ def project_tangent(geom: LensGeometry, i, x, p, S, dx, dp, dS):
         iu, iv = np.floor(u).astype(np.int64), np.floor(v).astype(np.int64)
         fu, fv = u - iu, v - iv
         for s, cs in enumerate(geom.chi_s):
-            inside = chic < cs
-            f = 1.0 / chic - 1.0 / cs
-            w = np.where(inside, K * f * inva, 0.0)
-            dw = np.where(inside, K * (-inva / chic ** 2 + f * dinva), 0.0) * dchic
+            if geom.nz[s] is None:
+                inside = chic < cs
+                f = 1.0 / chic - 1.0 / cs
+                w = np.where(inside, K * f * inva, 0.0)
+                dw = np.where(inside, K * (-inva / chic ** 2 + f * dinva), 0.0) * dchic
+            else:
+                q, dq = geom.source_weight(s, chic)
+                w = K * q / chic * inva
+                dw = K * ((dq * chic - q) / chic ** 2 * inva + q / chic * dinva) * dchic
             for du in (0, 1):
                 for dv in (0, 1):
                     wu = fu if du else 1.0 - fu

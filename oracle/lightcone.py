@@ -125,6 +125,45 @@ class LensGeometry:
         self.chi_a = cosmo.chi(stepper.a)  # chi at every step boundary
         self.prefac = 1.5 * cosmo.omega_m / C_OVER_H0 ** 2
         self.vp = (self.box / self.nc) ** 3
+        self.nz = [None] * len(self.zs)      # per source: None (a plane at zs) or (z, n, tables)
+
+    def set_source_nz(self, s, z, n):
+        """Source s becomes the distribution n(z) (Eq. conv with a general n(chi')):
+        n tabulated at ascending redshifts z, linear in between and zero outside,
+        normalised to unit integral over z.  Its lensing efficiency is
+
+            q(chi) = int dz' n(z') (1 - chi / chi(z'))_+ = A(chi) - chi B(chi),
+            A(chi) = int_{z(chi)} n dz',  B(chi) = int_{z(chi)} n / chi(z') dz',
+
+        and dq/dchi = -B(chi) (the boundary terms cancel).  A and B are cumulative
+        trapezoid integrals from the top on a 200001-point redshift grid.
+        """
+        z = np.asarray(z, dtype=np.float64)
+        n = np.asarray(n, dtype=np.float64)
+        zz = np.linspace(z[0], z[-1], 200001)
+        nn = np.interp(zz, z, n)
+        nn = nn / float(np.sum(0.5 * (nn[1:] + nn[:-1]) * np.diff(zz)))
+        chi = self.cosmo.chi_z(zz)
+
+        def cum_top(f):      # int_{zz[k]}^{zz[-1]} f dz'
+            seg = 0.5 * (f[1:] + f[:-1]) * np.diff(zz)
+            return np.concatenate([np.cumsum(seg[::-1])[::-1], [0.0]])
+        A = cum_top(nn)
+        B = cum_top(np.where(chi > 0, nn / np.where(chi > 0, chi, 1.0), 0.0))
+        self.nz[s] = (z, n, chi, A, B)
+        self.chi_s[s] = chi[-1]          # farthest contributing distance
+
+    def source_weight(self, s, chi):
+        """(q_s(chi), dq_s/dchi): the lensing efficiency of source s at comoving chi."""
+        chi = np.asarray(chi, dtype=np.float64)
+        if self.nz[s] is None:
+            cs = self.chi_s[s]
+            inside = chi < cs
+            return np.where(inside, (cs - chi) / cs, 0.0), np.where(inside, -1.0 / cs, 0.0)
+        _, _, cg, A, B = self.nz[s]
+        a = np.interp(chi, cg, A, left=A[0], right=0.0)
+        b = np.interp(chi, cg, B, left=B[0], right=0.0)
+        return np.maximum(a - chi * b, 0.0), -b
 
     def shell(self, i):
         return self.chi_a[i + 1], self.chi_a[i]
@@ -134,11 +173,15 @@ class LensGeometry:
         return lo < self.chi_s.max()
 
     def mean_term(self):
-        """(3/2) Om (H0/c)^2 int_0^chi_s chi (chi_s - chi) / (chi_s a(chi)) dchi."""
+        """(3/2) Om (H0/c)^2 int_0^chi_s chi (chi_s - chi) / (chi_s a(chi)) dchi, or with a
+        source distribution (3/2) Om (H0/c)^2 int chi q(chi) / a(chi) dchi."""
         out = []
-        for cs in self.chi_s:
-            f = lambda c: c * (cs - c) / (cs * self.cosmo.a_of_chi(c))  # noqa: E731
-            v, _ = quad(f, 0.0, cs, limit=500, epsabs=0, epsrel=1e-12)
+        for s, cs in enumerate(self.chi_s):
+            if self.nz[s] is None:
+                f = lambda c: c * (cs - c) / (cs * self.cosmo.a_of_chi(c))  # noqa: E731
+            else:
+                f = lambda c, s=s: c * float(self.source_weight(s, c)[0]) / self.cosmo.a_of_chi(c)  # noqa: E731
+            v, _ = quad(f, 0.0, cs, limit=2000, epsabs=0, epsrel=1e-12)
             out.append(self.prefac * v)
         return np.array(out)
 
@@ -199,8 +242,11 @@ class LensGeometry:
         fu, fv = u - iu, v - iv
         omega_pix = self.dtheta ** 2
         for s, cs in enumerate(self.chi_s):
-            w = np.where(chic < cs,
-                         self.prefac * (cs - chic) / (cs * chic * ac) * self.vp / omega_pix, 0.0)
+            if self.nz[s] is None:
+                w = np.where(chic < cs,
+                             self.prefac * (cs - chic) / (cs * chic * ac) * self.vp / omega_pix, 0.0)
+            else:
+                w = self.prefac * self.source_weight(s, chic)[0] / (chic * ac) * self.vp / omega_pix
             for du in (0, 1):
                 for dv in (0, 1):
                     ww = w * (fu if du else 1.0 - fu) * (fv if dv else 1.0 - fv)

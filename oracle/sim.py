@@ -22,7 +22,7 @@ class Simulation:
     def __init__(self, nc, nmesh, box, a_init, nsteps, zs, map_npix, map_fov_deg,
                  omega_m, sigma8, h=0.6774, n_s=0.9667, omega_b=0.0486, t_cmb=2.7255,
                  lpt_order=1, sub_evolution=1, pgd=0, pgd_params=(0.0, 0.0, 0.1, 1.0, 4.0),
-                 rotate=1, rotation_seed=42, cosmo=None, **_ignored):
+                 rotate=1, rotation_seed=42, cosmo=None, source_nz=None, **_ignored):
         self.nc, self.nmesh, self.box = int(nc), int(nmesh), float(box)
         self.nsteps, self.lpt_order = int(nsteps), int(lpt_order)
         self.cosmo = cosmo or Cosmology(omega_m, sigma8, h, n_s, omega_b, t_cmb,
@@ -31,6 +31,9 @@ class Simulation:
         self.geom = LensGeometry(self.cosmo, self.stepper, zs, map_npix, map_fov_deg,
                                  box, nc, nmesh, rotate=rotate, seed=rotation_seed,
                                  sub_evolution=sub_evolution)
+        # source_nz: {plane index: (z, n)} -- those planes become distributions n(z)
+        for s_, (z, n) in (source_nz or {}).items():
+            self.geom.set_source_nz(int(s_), z, n)
         self.pgd = bool(pgd)
         self.pgd_params = tuple(pgd_params)
         self.maps = np.zeros((len(self.geom.zs), self.geom.npix, self.geom.npix))
