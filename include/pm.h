@@ -136,6 +136,19 @@ pm_status kappa_maps(pm_ctx* ctx, double* d_maps);
 pm_status pm_vjp(pm_ctx* ctx, const double* d_dL_dkappa, double* d_dL_dnoise,
                  double* h_dL_dparams);
 
+/* Replace source plane s (0 <= s < n_zs) by a distribution of source
+ * redshifts (Eq. conv with a general n(chi')): n tabulated at npts >= 2
+ * strictly ascending redshifts h_z (host arrays, 0 < z < 1/a_init - 1),
+ * n >= 0, linear in between and zero outside, normalised to unit integral.
+ * Map s then weights each projected particle by the lensing efficiency
+ * q(chi) = int dz' n(z') (1 - chi / chi(z'))_+ instead of (chi_s - chi)/chi_s,
+ * and its mean-density term becomes (3/2) Om (H0/c)^2 int chi q / a dchi.
+ * Builds the host FP64 tables (and their Omega_m +/- h versions when the
+ * derivatives are configured).  Call after pm_init and before the first
+ * lens_project of a run (PM_ERR_STATE otherwise); PM_ERR_ARG on invalid
+ * tables.  Synchronises the stream. */
+pm_status pm_set_source_nz(pm_ctx* ctx, int32_t s, const double* h_z, const double* h_n, int32_t npts);
+
 /* Forward-mode derivative (JVP) of the maps along a direction of the initial
  * white noise (Sec. 3: the model is differentiable in the initial modes; the
  * paper checks its Jacobian-vector product by changing the initial field in

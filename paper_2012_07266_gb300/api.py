@@ -41,6 +41,18 @@ class Simulation:
         self.nsteps = self.cfg.nsteps
         self.n_zs = self.cfg.n_zs
         self.npix = self.cfg.map_npix
+        # source planes replaced by distributions n(z): {plane index: (z, n)}
+        for s, (z, n) in (workload.get("source_nz") or {}).items():
+            self.set_source_nz(int(s), z, n)
+
+    def set_source_nz(self, s: int, z, n):
+        """Source plane s becomes the distribution n(z) (host arrays; see pm_set_source_nz)."""
+        z = [float(v) for v in z]
+        n = [float(v) for v in n]
+        if len(z) != len(n):
+            raise ValueError("z and n(z) differ in length")
+        zt, nt = (C.c_double * len(z))(*z), (C.c_double * len(n))(*n)
+        lib.call("pm_set_source_nz", self.ctx, int(s), C.cast(zt, C.c_void_p), C.cast(nt, C.c_void_p), len(z))
 
     def __del__(self):
         ctx = getattr(self, "ctx", None)

@@ -314,11 +314,21 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
       const R dinva = interp_t<R>(A.tab_dinva, A.tab_n, (R)A.tab_hinv, cd);
       R grc[3] = {0, 0, 0};
       for (int s = 0; s < A.nzs; ++s) {
-        const R csd = (R)A.chi_s[s];
-        if (!(cd < csd)) continue;
-        const R fr = R(1) / cd - R(1) / csd;
-        const R w = (R)A.wpref * fr * inva;
-        const R dw = (R)A.wpref * (-inva / (cd * cd) + fr * dinva);
+        R w, dw;
+        if (A.nz_mask >> s & 1u) {
+          // source distribution: w = wpref q / (chi a), dw/dchi from q and dq/dchi
+          const R qv = interp_t<R>(A.qtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, cd);
+          if (!(qv > R(0))) continue;
+          const R dqv = interp_t<R>(A.dqtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, cd);
+          w = (R)A.wpref * qv / cd * inva;
+          dw = (R)A.wpref * ((dqv * cd - qv) / (cd * cd) * inva + qv / cd * dinva);
+        } else {
+          const R csd = (R)A.chi_s[s];
+          if (!(cd < csd)) continue;
+          const R fr = R(1) / cd - R(1) / csd;
+          w = (R)A.wpref * fr * inva;
+          dw = (R)A.wpref * (-inva / (cd * cd) + fr * dinva);
+        }
         const double* lam = A.lam + s * A.npix * A.npix;
         R Lw = 0, Lu = 0, Lv = 0;
 #pragma unroll

@@ -24,6 +24,8 @@ struct LensAdjArgs {
   double wpref, d1_next, inv_gp_half, tab_hinv;
   int tab_n;
   const R *tab_d1, *tab_dd1, *tab_inva, *tab_dinva;  // path precision
+  unsigned nz_mask;         // bit s: source s is a distribution n(z)
+  const R *qtab, *dqtab;    // its q(chi) and dq/dchi, n_zs x tab_n
   const double* lam;  // dL/dkappa, n_zs * npix^2
   R* lx;              // d/dx accumulators (cells), 3 * np
   R* lp;              // d/dp accumulators (cells), 3 * np
@@ -66,7 +68,7 @@ void adj_lens(const LensAdjArgs<R>& A, cudaStream_t st, Prof* pf);
 // One cosmology of a lens dot product: chi tables (TabId), source distances,
 // weight prefactor, the shell's D1(a_{i+1}) and g_p(a_{i+1/2}), accumulator.
 struct LensDotVar {
-  int tab_d1, tab_inva;
+  int tab_d1, tab_inva, qkind;  // TabIds, QKind of the n(z) tables
   const double* chi_s;
   double wpref, d1_next, gp_half;
   double* acc;

@@ -59,6 +59,8 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
   L.tab_d1 = o; o += al(kChiTab * 8);
   L.tab_inva = o; o += al(kChiTab * 8);
   L.ftab = o; o += T_COUNT * al(kChiTab * 4);
+  L.qtab = o; o += al((size_t)4 * cfg.n_zs * kChiTab * 8);    // n(z) sources: q, dq, q(+h), q(-h)
+  L.qtab_f = o; o += al((size_t)4 * cfg.n_zs * kChiTab * 4);
   L.scratch = o;
   const int nout = cfg.pgd ? 6 : 3;
   L.rho = o;
@@ -174,6 +176,105 @@ void build_tables(pm_ctx* c) {
     }
     c->mean_term[s] = 1.5 * cfg.omega_m / (kCoverH0 * kCoverH0) * acc * hh / 3.0;
   }
+}
+
+// ------------------------------------------------------ source distributions
+// Lensing efficiency of a normalised, piecewise-linear n(z) (Eq. conv with a
+// distribution of source distances) on the chi grid of the lens tables:
+//   q(chi) = int dz' n(z') (1 - chi / chi(z'))_+ = A(chi) - chi B(chi),
+//   A = int_{z(chi)} n dz',  B = int_{z(chi)} n / chi(z') dz',  dq/dchi = -B,
+// with A and B cumulative trapezoid integrals from the top on a 20001-point
+// redshift grid.  Returns the farthest contributing distance in chimax.
+void nz_tables(const pm_ctx* c, const Cosmo& co, const std::vector<double>& z, const std::vector<double>& n,
+               std::vector<double>& q, std::vector<double>& dq, double& chimax) {
+  const int G = 20001;
+  std::vector<double> zz(G), nn(G), ch(G), A(G), B(G);
+  const double z0 = z.front(), z1 = z.back();
+  size_t seg = 0;
+  for (int k = 0; k < G; ++k) {
+    zz[k] = z0 + (z1 - z0) * k / (G - 1);
+    while (seg + 2 < z.size() && z[seg + 1] < zz[k]) ++seg;
+    const double t = std::min(std::max((zz[k] - z[seg]) / (z[seg + 1] - z[seg]), 0.0), 1.0);
+    nn[k] = n[seg] + t * (n[seg + 1] - n[seg]);
+    ch[k] = co.chi_a(1.0 / (1.0 + zz[k]));
+  }
+  double norm = 0.0;
+  for (int k = 0; k + 1 < G; ++k) norm += 0.5 * (nn[k] + nn[k + 1]) * (zz[k + 1] - zz[k]);
+  A[G - 1] = B[G - 1] = 0.0;
+  for (int k = G - 2; k >= 0; --k) {
+    const double dz = zz[k + 1] - zz[k];
+    A[k] = A[k + 1] + 0.5 * (nn[k] + nn[k + 1]) * dz / norm;
+    B[k] = B[k + 1] + 0.5 * (nn[k] / ch[k] + nn[k + 1] / ch[k + 1]) * dz / norm;
+  }
+  chimax = ch[G - 1];
+  q.assign(kChiTab, 0.0);
+  dq.assign(kChiTab, 0.0);
+  int j = 0;
+  for (int k = 0; k < kChiTab; ++k) {
+    const double x = k * c->chi_tab_h;
+    double a = 0.0, b = 0.0;
+    if (x <= ch[0]) {
+      a = A[0];
+      b = B[0];
+    } else if (x < ch[G - 1]) {
+      while (ch[j + 1] < x) ++j;
+      const double t = (x - ch[j]) / (ch[j + 1] - ch[j]);
+      a = A[j] + t * (A[j + 1] - A[j]);
+      b = B[j] + t * (B[j + 1] - B[j]);
+    }
+    q[k] = std::max(a - x * b, 0.0);
+    dq[k] = -b;
+  }
+}
+
+// (3/2) Om (H0/c)^2 int_0^chimax chi q(chi) / a(chi) dchi on the table grid (trapezoid)
+double nz_mean_term(const pm_ctx* c, const Cosmo& co, double om, const std::vector<double>& q) {
+  std::vector<double> ag(kChiTab);
+  co.a_of_chi_grid(c->chi_tab_h, kChiTab, ag.data());
+  double acc = 0.0;
+  for (int k = 0; k + 1 < kChiTab; ++k) {
+    const double x0 = k * c->chi_tab_h, x1 = (k + 1) * c->chi_tab_h;
+    acc += 0.5 * (x0 * q[k] / ag[k] + x1 * q[k + 1] / ag[k + 1]) * c->chi_tab_h;
+  }
+  return 1.5 * om / (kCoverH0 * kCoverH0) * acc;
+}
+
+// build and upload source s's tables (central cosmology, and the Omega_m +/- h
+// pair when the derivative tables exist); the source's distance becomes chimax
+cudaError_t set_nz_tables(pm_ctx* c, int s) {
+  const pm_config& cfg = c->cfg;
+  const bool deriv = cfg.ckpt_every > 0 || cfg.jvp;
+  std::vector<double> tab[4];
+  double chimax = 0.0, chip = 0.0, chim = 0.0;
+  nz_tables(c, c->cosmo, c->nz_z[s], c->nz_n[s], tab[Q_CENTRAL], tab[Q_DERIV], chimax);
+  c->chi_s[s] = chimax;
+  c->mean_term[s] = nz_mean_term(c, c->cosmo, cfg.omega_m, tab[Q_CENTRAL]);
+  std::vector<double> unused;
+  if (deriv) {
+    nz_tables(c, c->cos_p, c->nz_z[s], c->nz_n[s], tab[Q_PLUS], unused, chip);
+    nz_tables(c, c->cos_m, c->nz_z[s], c->nz_n[s], tab[Q_MINUS], unused, chim);
+    c->chi_s_p[s] = chip;
+    c->chi_s_m[s] = chim;
+    c->mean_p[s] = nz_mean_term(c, c->cos_p, cfg.omega_m + c->adj_h, tab[Q_PLUS]);
+    c->mean_m[s] = nz_mean_term(c, c->cos_m, cfg.omega_m - c->adj_h, tab[Q_MINUS]);
+  } else {
+    tab[Q_PLUS].assign(kChiTab, 0.0);
+    tab[Q_MINUS].assign(kChiTab, 0.0);
+  }
+  const size_t per = (size_t)cfg.n_zs * kChiTab;
+  for (int kind = 0; kind < 4; ++kind) {
+    const size_t at = (size_t)kind * per + (size_t)s * kChiTab;
+    cudaError_t e = cudaMemcpyAsync(c->ws + c->L.qtab + at * 8, tab[kind].data(), kChiTab * 8,
+                                    cudaMemcpyHostToDevice, c->stream);
+    if (e) return e;
+    std::vector<float> f(tab[kind].begin(), tab[kind].end());
+    if ((e = cudaMemcpyAsync(c->ws + c->L.qtab_f + at * 4, f.data(), kChiTab * 4, cudaMemcpyHostToDevice,
+                             c->stream)))
+      return e;
+    if ((e = cudaStreamSynchronize(c->stream))) return e;  // the host vectors go out of scope
+  }
+  c->nz_mask |= 1u << s;
+  return cudaSuccess;
 }
 
 // FP32 mirror of a chi table, uploaded beside the FP64 one
@@ -716,6 +817,9 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
         A.tab_dd1 = chi_table<R>(c, T_DD1);
         A.tab_inva = chi_table<R>(c, T_INVA);
         A.tab_dinva = chi_table<R>(c, T_DINVA);
+        A.nz_mask = c->nz_mask;
+        A.qtab = qtable<R>(c, Q_CENTRAL);
+        A.dqtab = qtable<R>(c, Q_DERIV);
         A.lam = lam;
         A.lx = lx;
         A.lp = lp;
@@ -730,9 +834,9 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
           adj_lens<R>(A, s, pf);
           shp.nrep = shm.nrep = A.nrep;
           for (int q = 0; q < A.nrep; ++q) shp.rep[q] = shm.rep[q] = A.rep[q];
-          const LensDotVar vp_ = {T_D1P, T_INVAP, c->chi_s_p.data(), wpref_p, shp.d1_next, shp.gp_half,
+          const LensDotVar vp_ = {T_D1P, T_INVAP, Q_PLUS, c->chi_s_p.data(), wpref_p, shp.d1_next, shp.gp_half,
                                   acc + 2 * n + i};
-          const LensDotVar vm_ = {T_D1M, T_INVAM, c->chi_s_m.data(), wpref_m, shm.d1_next, shm.gp_half,
+          const LensDotVar vm_ = {T_D1M, T_INVAM, Q_MINUS, c->chi_s_m.data(), wpref_m, shm.d1_next, shm.gp_half,
                                   acc + 3 * n + i};
           if (launch_lens_dot2<R>(c, shp, pg, lam, vp_, vm_)) return PM_ERR_CUDA;
         }
@@ -1101,6 +1205,22 @@ pm_status pm_vjp(pm_ctx* c, const double* d_dL_dkappa, double* d_dL_dnoise, doub
   c->last_stepped = -1;
   c->vjp_state_lost = 1;
   return st;
+}
+
+pm_status pm_set_source_nz(pm_ctx* c, int32_t s, const double* h_z, const double* h_n, int32_t npts) {
+  if (!c || !h_z || !h_n || s < 0 || s >= c->cfg.n_zs || npts < 2 || npts > 100000) return PM_ERR_ARG;
+  if (c->projected >= 0) return PM_ERR_STATE;
+  const double zmax = 1.0 / c->cfg.a_init - 1.0;
+  double area = 0.0;
+  for (int k = 0; k < npts; ++k) {
+    if (!std::isfinite(h_z[k]) || !std::isfinite(h_n[k]) || h_n[k] < 0.0) return PM_ERR_ARG;
+    if (k > 0 && !(h_z[k] > h_z[k - 1])) return PM_ERR_ARG;
+    if (k > 0) area += 0.5 * (h_n[k] + h_n[k - 1]) * (h_z[k] - h_z[k - 1]);
+  }
+  if (!(h_z[0] > 0.0) || !(h_z[npts - 1] < zmax) || !(area > 0.0)) return PM_ERR_ARG;
+  c->nz_z[s].assign(h_z, h_z + npts);
+  c->nz_n[s].assign(h_n, h_n + npts);
+  return cuda_status(set_nz_tables(c, s));
 }
 
 pm_status pm_jvp(pm_ctx* c, const double* d_noise, const double* d_dnoise, double* d_kappa, double* d_dkappa) {

@@ -176,6 +176,8 @@ struct LensTanArgs {
   double wpref, d1_next, inv_gp_half, tab_hinv;
   int tab_n;
   const R *tab_d1, *tab_dd1, *tab_inva, *tab_dinva;
+  unsigned nz_mask;       // bit s: source s is a distribution n(z)
+  const R *qtab, *dqtab;  // its q(chi) and dq/dchi, n_zs x tab_n
   double* dmaps;
   int nrep;
   Replica rep[kMaxReplicas];
@@ -284,11 +286,21 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
       const R inva = interp_tab<R>(A.tab_inva, A.tab_n, (R)A.tab_hinv, chic);
       const R dinva = interp_tab<R>(A.tab_dinva, A.tab_n, (R)A.tab_hinv, chic);
       for (int s = 0; s < A.nzs; ++s) {
-        const R csd = (R)A.chi_s[s];
-        if (!(chic < csd)) continue;
-        const R fq = R(1) / chic - R(1) / csd;
-        const R w = (R)A.wpref * fq * inva;
-        const R dw = (R)A.wpref * (-inva / (chic * chic) + fq * dinva) * dchic;
+        R w, dw;
+        if (A.nz_mask >> s & 1u) {
+          // source distribution: w = wpref q / (chi a)
+          const R qv = interp_tab<R>(A.qtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, chic);
+          if (!(qv > R(0))) continue;
+          const R dqv = interp_tab<R>(A.dqtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, chic);
+          w = (R)A.wpref * qv / chic * inva;
+          dw = (R)A.wpref * ((dqv * chic - qv) / (chic * chic) * inva + qv / chic * dinva) * dchic;
+        } else {
+          const R csd = (R)A.chi_s[s];
+          if (!(chic < csd)) continue;
+          const R fq = R(1) / chic - R(1) / csd;
+          w = (R)A.wpref * fq * inva;
+          dw = (R)A.wpref * (-inva / (chic * chic) + fq * dinva) * dchic;
+        }
         const int off = s * A.npix * A.npix;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
@@ -409,6 +421,9 @@ cudaError_t launch_tan_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
   A.tab_dd1 = chi_table<R>(c, T_DD1);
   A.tab_inva = chi_table<R>(c, T_INVA);
   A.tab_dinva = chi_table<R>(c, T_DINVA);
+  A.nz_mask = c->nz_mask;
+  A.qtab = qtable<R>(c, Q_CENTRAL);
+  A.dqtab = qtable<R>(c, Q_DERIV);
   A.dmaps = reinterpret_cast<double*>(c->ws + c->L.tan_maps);
   A.nrep = sh.nrep;
   for (int q = 0; q < sh.nrep; ++q) A.rep[q] = sh.rep[q];

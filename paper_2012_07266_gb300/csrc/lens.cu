@@ -26,6 +26,7 @@ struct LensVar {
   double chi_s[PM_MAX_ZS];
   double wpref;       // (3/2) Om (H0/c)^2 V_p / Omega_pix
   double d1_next, inv_gp_half;
+  const R* qtab;      // q(chi) of the n(z) sources, n_zs x tab_n (sources in nz_mask)
   double* acc;
 };
 
@@ -45,6 +46,7 @@ struct LensArgs {
   double tab_hinv;
   int tab_n;
   LensVar<R> var[2];  // var[0]; dot mode may add a second cosmology (var[1]) on the same selection
+  unsigned nz_mask;   // bit s: source s is a distribution n(z) (weight from var.qtab)
   double* maps;
   int* flag;
   const double* lam;  // when set: accumulate sum(lam * increment) into var[v].acc instead of the maps
@@ -192,9 +194,16 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         const R cw[4] = {(R(1) - fu) * (R(1) - fv), fu * (R(1) - fv), (R(1) - fu) * fv, fu * fv};
         const R wk = (R)V.wpref * inva / chic;
         for (int s = 0; s < A.nzs; ++s) {
-          const R cs_ = (R)V.chi_s[s];
-          if (!(chic < cs_)) continue;
-          const R w = wk * (cs_ - chic) / cs_;
+          R w;
+          if (A.nz_mask >> s & 1u) {  // source distribution: w = wpref q(chi_c) / (chi_c a)
+            const R qv = interp<R>(V.qtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, chic);
+            if (!(qv > R(0))) continue;
+            w = wk * qv;
+          } else {  // source plane at chi_s
+            const R cs_ = (R)V.chi_s[s];
+            if (!(chic < cs_)) continue;
+            w = wk * (cs_ - chic) / cs_;
+          }
           const int off = s * A.npix * A.npix;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
@@ -269,6 +278,7 @@ cudaError_t launch_lens_dot2(pm_ctx* c, const LensShell& sel, int use_pgd, const
     V.tab_inva = chi_table<R>(c, in[v]->tab_inva);
     for (int s = 0; s < PM_MAX_ZS; ++s) V.chi_s[s] = s < c->cfg.n_zs ? in[v]->chi_s[s] : 0.0;
     V.wpref = in[v]->wpref;
+    V.qtab = qtable<R>(c, in[v]->qkind);
     V.d1_next = in[v]->d1_next;
     V.inv_gp_half = 1.0 / in[v]->gp_half;
     V.acc = in[v]->acc;
@@ -316,6 +326,7 @@ static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs
   V.inv_gp_half = 1.0 / sh.gp_half;
   V.tab_d1 = chi_table<R>(c, T_D1);
   V.tab_inva = chi_table<R>(c, T_INVA);
+  V.qtab = qtable<R>(c, Q_CENTRAL);
   V.acc = nullptr;
   A.var[1] = V;
   A.sub = c->cfg.sub_evolution;
@@ -323,6 +334,7 @@ static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs
   A.tab_n = kChiTab;
   A.maps = reinterpret_cast<double*>(c->ws + c->L.maps);
   A.flag = flags_ptr(c);
+  A.nz_mask = c->nz_mask;
   A.lam = nullptr;
   A.nrep = sh.nrep;
   for (int q = 0; q < sh.nrep; ++q) A.rep[q] = sh.rep[q];

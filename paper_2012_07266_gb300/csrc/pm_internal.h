@@ -106,6 +106,7 @@ struct Layout {
   size_t adj;
   size_t state_bytes;       // one particle state: cell | frac x3 | mom x3
   size_t tan_x, tan_p, tan_tmp, tan_f, tan_s, tan_maps, tan_ic;
+  size_t qtab, qtab_f;  // lensing efficiency tables of n(z) sources: FP64 and FP32 mirror
   size_t adj_noise, adj_ckpt, adj_seg, adj_fseg, adj_sseg, adj_lx, adj_lp, adj_v, adj_vs, adj_paint, adj_ic;
   size_t tab_dd1, tab_dinva, tab_d1p, tab_d1m, tab_invap, tab_invam, sqrtp_p, sqrtp_m, adj_acc;
   int nck, nic;             // checkpoints, IC adjoint fields
@@ -139,6 +140,9 @@ struct pm_ctx {
   pmlens::Cosmo cos_p, cos_m;
   std::vector<double> kick_p, kick_m, drift_p, drift_m, chi_s_p, chi_s_m;
   double mean_p[PM_MAX_ZS], mean_m[PM_MAX_ZS];
+  // source distributions (pm_set_source_nz): bit s set when source s is n(z)
+  unsigned nz_mask = 0;
+  std::vector<double> nz_z[PM_MAX_ZS], nz_n[PM_MAX_ZS];
   int next_step;     // next pm_step index; -1 before pm_ic
   int last_stepped;  // index of the last pm_step, -1 none
   int projected;     // last projected shell
@@ -256,6 +260,15 @@ inline const R* chi_table(pm_ctx* c, int id) {
 }
 inline int* flags_ptr(pm_ctx* c) { return reinterpret_cast<int*>(c->ws + c->L.flags); }
 inline int* timeout_ptr(pm_ctx* c) { return flags_ptr(c) + 1; }
+// q tables of the n(z) sources, kind 0: q(chi), 1: dq/dchi, 2: q at Omega_m + h, 3: at
+// Omega_m - h; n_zs * kChiTab entries per kind (source s at s * kChiTab)
+enum QKind { Q_CENTRAL = 0, Q_DERIV = 1, Q_PLUS = 2, Q_MINUS = 3 };
+template <typename R>
+inline const R* qtable(pm_ctx* c, int kind) {
+  const size_t n = (size_t)c->cfg.n_zs * kChiTab;
+  if constexpr (sizeof(R) == 8) return reinterpret_cast<const R*>(c->ws + c->L.qtab) + kind * n;
+  else return reinterpret_cast<const R*>(c->ws + c->L.qtab_f) + kind * n;
+}
 inline size_t fmesh_at(const pm_ctx* c) { return c->f_at ? c->f_at : c->L.fmesh; }
 inline size_t smesh_at(const pm_ctx* c) { return c->s_at ? c->s_at : c->L.smesh; }
 
