@@ -17,6 +17,8 @@ quadrature, ODE integration, interpolation), following the paper's method:
   finite-difference cosmology derivatives (``cosmology``, ``adjoint``)
 * Sec. 3 / Fig. 8 -- the forward-mode derivative along a noise direction
   (``jvp``), pinned to the reverse sweep by the dot-product identity
+* Sec. 4 (Fig. accuracy) -- shot-noise runs with uniformly random particles and
+  the flat-sky angular power spectrum of the maps (``shotnoise``)
 
 Readings of points the paper leaves open are stated in each function's
 docstring.  Parity unpinned: absolute Eisenstein-Hu transfer values (only

@@ -117,6 +117,7 @@ class LensGeometry:
         self.zs = np.atleast_1d(np.asarray(zs, dtype=np.float64))
         self.chi_s = cosmo.chi_z(self.zs)
         self.npix = int(npix)
+        self.fov_deg = float(fov_deg)
         self.fov = np.deg2rad(fov_deg)
         self.dtheta = self.fov / self.npix
         self.box, self.nc, self.nmesh = float(box), int(nc), int(nmesh)
