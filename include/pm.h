@@ -162,6 +162,49 @@ pm_status pm_set_source_nz(pm_ctx* ctx, int32_t s, const double* h_z, const doub
  * Synchronises the stream; PM_ERR_NONFINITE as kappa_maps. */
 pm_status pm_jvp(pm_ctx* ctx, const double* d_noise, const double* d_dnoise, double* d_kappa, double* d_dkappa);
 
+/* Shot-noise run (Sec. 4, Fig. accuracy: the shot noise of the maps is
+ * estimated from runs with randomly placed particles, whose averaged power
+ * spectrum is subtracted).  Places the nc^3 particles i.i.d. uniform in the
+ * box -- coordinate k of particle j from output 3j + k of the SplitMix64
+ * sequence seeded with `seed` (output n mixes the state
+ * seed + (n + 1) * 0x9E3779B97F4A7C15), its top 24 bits r giving x = L r / 2^24
+ * -- with zero momentum and without PGD, projects every shell of the
+ * lightcone as lens_project would (replicas, rotations, source planes or
+ * distributions), subtracts the mean-density terms and writes the maps
+ * (n_zs * npix^2 float64, device, caller-owned, layout as kappa_maps) to
+ * d_kappa.  The context's particle state, maps and derivative records are
+ * overwritten: pm_step, lens_project, kappa_maps, pm_vjp and the inspection
+ * calls return PM_ERR_STATE until the next pm_ic.  Synchronises the stream;
+ * PM_ERR_NONFINITE as kappa_maps. */
+pm_status pm_shot_noise_maps(pm_ctx* ctx, uint64_t seed, double* d_kappa);
+
+/* Workspace bytes pm_map_cl needs for nmaps maps of npix^2 pixels and nbins
+ * bins (PM_ERR_ARG where pm_map_cl would refuse the sizes). */
+pm_status pm_map_cl_workspace_size(int32_t npix, int32_t nmaps, int32_t nbins, size_t* bytes);
+
+/* Binned flat-sky angular power spectrum of maps (Sec. 4, Fig. accuracy: the
+ * convergence power spectra and the shot noise subtracted from them).  Needs
+ * no context.  For map m (d_maps + m npix^2, float64 [iy][ix], device) and
+ * every DFT mode (m_x, m_y), each in -npix/2 .. npix/2 - 1, with
+ * FOV_rad = fov_deg * (pi / 180) and Omega_pix = (FOV_rad / npix)^2:
+ *   C = Omega_pix |sum_j kappa_j exp(-2 pi i (m_x ix + m_y iy) / npix)|^2 / npix^2,
+ *   l = (2 pi / FOV_rad) * sqrt(m_x^2 + m_y^2)   (IEEE double, in this order);
+ * the value of bin b is the mean of C over the modes with
+ * h_edges[b] <= l < h_edges[b+1] (0 for a bin without modes), and
+ *   d_cl[m * nbins + b] = beta * d_cl[m * nbins + b] + alpha * value
+ * (beta = 0 ignores the old contents; beta = 1, alpha = -1/R subtracts the mean
+ * of R spectra, e.g. of shot-noise runs).  npix a power of two in [8, 4096],
+ * 1 <= nmaps, 1 <= nbins <= 2048, h_edges (host, nbins + 1 values) strictly
+ * ascending (the last may be +inf), fov_deg > 0: PM_ERR_ARG otherwise.
+ * d_workspace: device, 256-byte aligned, at least pm_map_cl_workspace_size
+ * bytes (PM_ERR_WORKSPACE otherwise).  h_counts: NULL, or host int64[nbins]
+ * receiving the number of modes of each bin (the call then synchronises the
+ * stream).  Enqueued on `stream` (a cudaStream_t; NULL: the legacy default
+ * stream).  FP64 throughout. */
+pm_status pm_map_cl(const double* d_maps, int32_t nmaps, int32_t npix, double fov_deg, const double* h_edges,
+                    int32_t nbins, double alpha, double beta, double* d_cl, int64_t* h_counts, void* d_workspace,
+                    size_t workspace_bytes, void* stream);
+
 /* Free the context (not the caller's workspace). */
 pm_status pm_destroy(pm_ctx* ctx);
 

@@ -20,6 +20,31 @@ def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
 
+def map_cl(maps: torch.Tensor, fov_deg: float, edges, alpha=1.0, beta=0.0, out=None, stream=None,
+           return_counts=False):
+    """Binned flat-sky angular power spectrum of maps (..., npix, npix) on their
+    GPU (pm_map_cl): out = beta * out + alpha * C(l) per map and bin; with
+    return_counts also the number of modes per bin."""
+    maps = maps.to(dtype=torch.float64).contiguous()
+    npix = int(maps.shape[-1])
+    nmaps = maps.numel() // (npix * npix)
+    edges = [float(e) for e in edges]
+    nb = len(edges) - 1
+    n = C.c_size_t(0)
+    lib.call("pm_map_cl_workspace_size", npix, nmaps, nb, C.byref(n))
+    stream = stream if stream is not None else torch.cuda.current_stream(maps.device)
+    ws = torch.empty(int(n.value), dtype=torch.uint8, device=maps.device)
+    ws.record_stream(stream)
+    if out is None:
+        out = torch.zeros(tuple(maps.shape[:-2]) + (nb,), dtype=torch.float64, device=maps.device)
+    eh = (C.c_double * (nb + 1))(*edges)
+    counts = (C.c_int64 * nb)() if return_counts else None
+    lib.call("pm_map_cl", _ptr(maps), nmaps, npix, float(fov_deg), C.cast(eh, C.c_void_p), nb, float(alpha),
+             float(beta), _ptr(out), C.cast(counts, C.c_void_p) if counts is not None else None, _ptr(ws),
+             C.c_size_t(n.value), C.c_void_p(stream.cuda_stream))
+    return (out, [int(v) for v in counts]) if return_counts else out
+
+
 class Simulation:
     """One forward (and optionally adjoint) lensing simulation on one GPU."""
 
@@ -108,6 +133,36 @@ class Simulation:
         hp = (C.c_double * 2)()
         lib.call("pm_vjp", self.ctx, _ptr(g), _ptr(dn), C.cast(hp, C.c_void_p))
         return dn, (hp[0], hp[1])
+
+    # -- shot noise (Sec. 4)
+    def shot_noise_maps(self, seed: int) -> torch.Tensor:
+        """Maps of one shot-noise run with uniformly random particles; replaces the
+        particle state (pm_ic starts the next simulation)."""
+        out = self._f64(self.n_zs, self.npix, self.npix)
+        lib.call("pm_shot_noise_maps", self.ctx, C.c_uint64(int(seed)), _ptr(out))
+        return out
+
+    def cl(self, maps: torch.Tensor, edges, **kw) -> torch.Tensor:
+        """Binned C(l) of maps of this field of view (see map_cl)."""
+        return map_cl(maps, self.cfg.map_fov_deg, edges, stream=self.stream, **kw)
+
+    def shot_noise_cl(self, edges, seeds) -> torch.Tensor:
+        """Mean binned C(l) of the shot-noise runs with the given seeds."""
+        seeds = list(seeds)
+        out = None
+        for k, sd in enumerate(seeds):
+            out = self.cl(self.shot_noise_maps(sd), edges, alpha=1.0 / len(seeds), beta=0.0 if k == 0 else 1.0,
+                          out=out)
+        return out
+
+    def cl_minus_shot_noise(self, kappa: torch.Tensor, edges, seeds) -> torch.Tensor:
+        """C(l) of the maps kappa minus the mean C(l) of shot-noise runs (Sec. 4,
+        Fig. accuracy); the runs replace the particle state."""
+        seeds = list(seeds)
+        out = self.cl(kappa, edges)
+        for sd in seeds:
+            self.cl(self.shot_noise_maps(sd), edges, alpha=-1.0 / len(seeds), beta=1.0, out=out)
+        return out
 
     # -- state transfer / inspection
     def particles(self):

@@ -34,6 +34,7 @@ UNITS = [
     ("adjoint.cu", "adjoint.o", []),
     ("sort.cu", "sort.o", []),
     ("jvp.cu", "jvp.o", []),
+    ("shotnoise.cu", "shotnoise.o", []),
 ]
 
 

@@ -591,6 +591,28 @@ pm_status do_lens(pm_ctx* c, int i) {
   return PM_OK;
 }
 
+pm_status read_flags(pm_ctx* c);
+
+// one shot-noise run (Sec. 4): uniformly random particles at rest, sorted for
+// the projection's replica culling, projected through every shell without PGD,
+// the mean-density terms subtracted
+template <typename R>
+pm_status do_shot_noise(pm_ctx* c, uint64_t seed, double* out) {
+  if (cudaMemsetAsync(c->ws + c->L.maps, 0, (size_t)c->cfg.n_zs * c->cfg.map_npix * c->cfg.map_npix * 8, c->stream))
+    return PM_ERR_CUDA;
+  if (launch_random_particles<R>(c, seed)) return PM_ERR_CUDA;
+  launch_iota(c);
+  if (sort_particles<R>(c)) return PM_ERR_CUDA;
+  c->pgd_valid = 0;
+  for (int i = 0; i < c->cfg.nsteps; ++i) {
+    if (!shell_active(c, i)) continue;
+    const pm_status st = do_lens<R>(c, i);
+    if (st) return st;
+  }
+  if (launch_kappa_finalize(c, out)) return PM_ERR_CUDA;
+  return read_flags(c);
+}
+
 template <typename R>
 __global__ void k_unpad_complex(const typename std::conditional<sizeof(R) == 4, float2, double2>::type* in,
                                 double* out, int n, int P) {
@@ -1230,6 +1252,19 @@ pm_status pm_jvp(pm_ctx* c, const double* d_noise, const double* d_dnoise, doubl
   c->tan_on = 0;
   c->tan_noise = nullptr;
   return st;
+}
+
+pm_status pm_shot_noise_maps(pm_ctx* c, uint64_t seed, double* d_kappa) {
+  if (!c || !d_kappa) return PM_ERR_ARG;
+  // the run replaces the particle state: no simulation continues from here
+  c->ic_done = 0;
+  c->next_step = -1;
+  c->last_stepped = -1;
+  c->projected = -1;
+  c->pgd_valid = 0;
+  c->vjp_state_lost = 1;
+  c->tan_on = 0;
+  return PM_DISPATCH(c, do_shot_noise, c, seed, d_kappa);
 }
 
 pm_status pm_destroy(pm_ctx* c) {

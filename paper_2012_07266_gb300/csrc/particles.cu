@@ -180,6 +180,32 @@ __global__ void k_set_particles(PState<R> s, const double* __restrict__ x, const
   }
 }
 
+// Uniformly random particles for a shot-noise run (Sec. 4): coordinate k of
+// particle j is output 3j + k of SplitMix64 seeded with `seed` (the state
+// seed + (n + 1) * gamma, mixed), whose top 24 bits r place it at
+// r M / 2^24 cells: integer cell (r M) >> 24 and the exact fraction of the
+// low 24 bits.  Zero momentum.
+template <typename R>
+__global__ void k_random_particles(PState<R> s, uint64_t seed, int M, long long np) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+    int ci[3];
+    R f[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      uint64_t z = seed + (uint64_t)(3 * j + k + 1) * 0x9E3779B97F4A7C15ULL;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+      z ^= z >> 31;
+      const uint64_t t = (z >> 40) * (uint64_t)M;
+      ci[k] = (int)(t >> 24);
+      f[k] = (R)((double)(t & 0xFFFFFFu) * 0x1p-24);
+    }
+    s.cell[j] = pack(ci[0], ci[1], ci[2]);
+    s.fx[j] = f[0]; s.fy[j] = f[1]; s.fz[j] = f[2];
+    s.px[j] = (R)0; s.py[j] = (R)0; s.pz[j] = (R)0;
+  }
+}
+
 template <typename R>
 __global__ void k_get_particles(PState<R> s, const uint32_t* __restrict__ pid, double* __restrict__ x,
                                 double* __restrict__ p, double len_per_cell, long long np) {
@@ -275,6 +301,13 @@ cudaError_t launch_set_particles(pm_ctx* c, const double* x, const double* p) {
 }
 
 template <typename R>
+cudaError_t launch_random_particles(pm_ctx* c, uint64_t seed) {
+  ProfScope ps(&c->prof, KK_IC, c->stream);
+  k_random_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(pstate<R>(c), seed, c->M, c->np);
+  return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_get_particles(pm_ctx* c, double* x, double* p) {
   ProfScope ps(&c->prof, KK_MISC, c->stream);
   k_get_particles<R><<<grid_for(c->np, 256), 256, 0, c->stream>>>(
@@ -310,6 +343,7 @@ cudaError_t launch_convert_out(const R* in, double* out, long long n, double sca
   template cudaError_t launch_readout<R>(pm_ctx*, R* const*, double, double*);                            \
   template cudaError_t launch_set_particles<R>(pm_ctx*, const double*, const double*);                    \
   template cudaError_t launch_get_particles<R>(pm_ctx*, double*, double*);                                \
+  template cudaError_t launch_random_particles<R>(pm_ctx*, uint64_t);                                     \
   template cudaError_t launch_lpt2_source<R>(pm_ctx*, R* const*, R*, long long);                          \
   template cudaError_t launch_convert_in<R>(const double*, R*, long long, cudaStream_t, Prof*);            \
   template cudaError_t launch_convert_out<R>(const R*, double*, long long, double, cudaStream_t, Prof*);

@@ -205,6 +205,8 @@ cudaError_t launch_readout(pm_ctx* c, R* const* meshes, double scale, double* ou
 template <typename R>
 cudaError_t launch_set_particles(pm_ctx* c, const double* x, const double* p);
 template <typename R>
+cudaError_t launch_random_particles(pm_ctx* c, uint64_t seed);
+template <typename R>
 cudaError_t launch_get_particles(pm_ctx* c, double* x, double* p);
 template <typename R>
 cudaError_t launch_lpt2_source(pm_ctx* c, R* const* d, R* src, long long n);

@@ -19,7 +19,8 @@ STATUS = {0: "PM_OK", 1: "PM_ERR_ARG", 2: "PM_ERR_WORKSPACE", 3: "PM_ERR_CUDA",
 
 # every symbol include/pm.h declares
 EXPORTS = ["pm_workspace_size", "pm_init", "pm_ic", "pm_step", "lens_project", "kappa_maps",
-           "pm_vjp", "pm_jvp", "pm_set_source_nz", "pm_destroy", "pm_strerror", "pm_get_particles", "pm_set_particles",
+           "pm_vjp", "pm_jvp", "pm_set_source_nz", "pm_shot_noise_maps", "pm_map_cl_workspace_size",
+           "pm_map_cl", "pm_destroy", "pm_strerror", "pm_get_particles", "pm_set_particles",
            "pm_get_forces", "pm_get_pgd", "pm_fft_r2c", "pm_get_density", "pm_sync_status",
            "pm_profile", "pm_profile_read", "pm_kernel_kinds", "pm_kernel_name",
            "pm_forces_static"]
@@ -96,6 +97,9 @@ def load():
         "pm_vjp": [vp, vp, vp, vp],
         "pm_jvp": [vp, vp, vp, vp, vp],
         "pm_set_source_nz": [vp, i32, vp, vp, i32],
+        "pm_shot_noise_maps": [vp, C.c_uint64, vp],
+        "pm_map_cl_workspace_size": [i32, i32, i32, C.POINTER(C.c_size_t)],
+        "pm_map_cl": [vp, i32, i32, C.c_double, vp, i32, C.c_double, C.c_double, vp, vp, vp, C.c_size_t, vp],
         "pm_destroy": [vp],
         "pm_get_particles": [vp, vp, vp],
         "pm_set_particles": [vp, vp, vp, i32],
