@@ -316,8 +316,9 @@ def run_gpu(a, rank, world, local_rank):
 
 
 def extra_legs(a, w, dev, rank):
-    """Forward + adjoint at the same workload, the plain FP64 path, and the
-    serving mix (Poisson arrivals, mixed sizes and cosmologies)."""
+    """Forward + adjoint at the same workload, forward mode, the plain FP64
+    path, the shot-noise estimate, and the serving mix (Poisson arrivals, mixed
+    sizes and cosmologies)."""
     import torch
 
     from paper_2012_07266_gb300.api import PM_FP32, PM_FP64, Simulation
@@ -382,6 +383,28 @@ def extra_legs(a, w, dev, rank):
     err = float((kappa32 - k64).norm() / k64.norm())
     out["plain_fp64"] = {"value": npart * nsteps / (t64 * 1e-3), "unit": UNIT, "ms_per_step": t64,
                          "fp32_speedup": t64 / out["fwd_adjoint"]["forward_ms"], "kappa_rel_l2_fp32_vs_fp64": err}
+    del sim
+    torch.cuda.empty_cache()
+    # shot-noise estimate (Sec. 4): random-position runs through the whole lightcone and the
+    # binned spectra of their maps (30 logarithmic bins, 100 <= l < 40000, plus l < 100)
+    sim = Simulation(device=dev, stream=stream, precision=PM_FP32, **w)
+    edges = np.concatenate([[0.0], np.geomspace(100.0, 40000.0, 30)])
+    m = sim.shot_noise_maps(0)
+    sim.cl(m, edges)
+    e2 = torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    for r in range(reps):
+        m = sim.shot_noise_maps(r + 1)
+    e1.record(stream)
+    for r in range(reps):
+        sim.cl(m, edges)
+    e2.record(stream)
+    e2.synchronize()
+    t_run, t_cl = e0.elapsed_time(e1) / reps, e1.elapsed_time(e2) / reps
+    out["shot_noise"] = {"run_ms": t_run, "cl_ms": t_cl, "maps": len(w["zs"]),
+                         "npix": w["map_npix"], "bins": len(edges) - 1,
+                         "run_over_forward": t_run / out["fwd_adjoint"]["forward_ms"]}
     del sim
     torch.cuda.empty_cache()
     # serving mix: Poisson arrivals at 20/s, meshes 64/128/192 (nc = mesh/2)

@@ -153,7 +153,6 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
   constexpr int T = N / V;
   constexpr int NB = V / RAD;
   constexpr int NR = N / RAD;
-  constexpr int TSTR = N / (NS * RAD);
   // unit-stride (padded) columns: constant offsets from one padded base per butterfly
   constexpr bool RD_CONST = RS == 1 && pad_step<NR, RAD, false, NS * RAD>(1) >= 0;
   constexpr bool WR_CONST = RS == 1 && pad_step<NS, RAD, true, NS * RAD>(1) >= 0;
@@ -187,7 +186,7 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
     if (NS > 1) {
 #pragma unroll
       for (int k = 1; k < RAD; ++k) {
-        C w = tw[jm * k * TSTR];
+        C w = tw[(k - 1) * NS + jm];
         if (INV) w.y = -w.y;
 #pragma unroll
         for (int cc = 0; cc < CP; ++cc) v[cc][b][k] = cmul(v[cc][b][k], w);
@@ -219,7 +218,8 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
 template <typename C, int N, int V, bool INV, int RS, int CS, int CP, int NS, int RAD, int... Rest>
 __device__ __forceinline__ void run_stages(C* buf, int col, int t, const C* tw) {
   stage<C, N, V, RAD, INV, NS, RS, CS, CP>(buf, col, t, tw);
-  if constexpr (sizeof...(Rest) > 0) run_stages<C, N, V, INV, RS, CS, CP, NS * RAD, Rest...>(buf, col, t, tw);
+  if constexpr (sizeof...(Rest) > 0)
+    run_stages<C, N, V, INV, RS, CS, CP, NS * RAD, Rest...>(buf, col, t, NS > 1 ? tw + (RAD - 1) * NS : tw);
 }
 
 template <typename C, int N, bool INV, int RS, int CS, int CP, int... Rs>
@@ -235,15 +235,33 @@ __device__ __forceinline__ void fft_column(C* buf, int col, int t, const C* tw) 
   fft_column_impl<C, N, INV, RS, CS, CP>(typename Plan<N>::Rad{}, buf, col, t, tw);
 }
 
-// tw[m] = exp(-2 pi i m / N), m < N
-template <typename C, int N> __device__ __forceinline__ void make_twiddles(C* tw) {
+// Stage-major twiddles of the plan of N: for each stage with NS > 1, in order,
+// the block tw[(k - 1) * NS + jm] = exp(-2 pi i jm k / (NS RAD)), k = 1..RAD-1,
+// jm < NS.  Threads that hold consecutive butterflies (consecutive jm) read
+// consecutive entries; in a table indexed by jm k N / (NS RAD) their reads
+// fell at strides that share banks.  N - RAD_1 entries in all (fewer than N).
+template <typename C, int NS, int RAD, int... Rest>
+__device__ __forceinline__ void fill_stage_twiddles(C* tw) {
   using R = decltype(C{}.x);
-  for (int m = threadIdx.x; m < N; m += blockDim.x) {
-    R s, c;
-    if constexpr (sizeof(R) == 4) sincospif(-2.0f * (float)m / (float)N, &s, &c);
-    else sincospi(-2.0 * (double)m / (double)N, &s, &c);
-    tw[m] = C{c, s};
+  if constexpr (NS > 1) {
+    for (int m = threadIdx.x; m < (RAD - 1) * NS; m += blockDim.x) {
+      const int k = m / NS + 1, jm = m - (k - 1) * NS;
+      R s, c;
+      if constexpr (sizeof(R) == 4) sincospif(-2.0f * (float)(jm * k) / (float)(NS * RAD), &s, &c);
+      else sincospi(-2.0 * (double)(jm * k) / (double)(NS * RAD), &s, &c);
+      tw[m] = C{c, s};
+    }
   }
+  if constexpr (sizeof...(Rest) > 0) fill_stage_twiddles<C, NS * RAD, Rest...>(NS > 1 ? tw + (RAD - 1) * NS : tw);
+}
+
+template <typename C, int... Rs>
+__device__ __forceinline__ void fill_plan_twiddles(Radices<Rs...>, C* tw) {
+  fill_stage_twiddles<C, 1, Rs...>(tw);
+}
+
+template <typename C, int N> __device__ __forceinline__ void make_twiddles(C* tw) {
+  fill_plan_twiddles<C>(typename Plan<N>::Rad{}, tw);
 }
 
 // tu[k] = exp(-2 pi i k / N), k <= N / 2 (real <-> half-length complex untangling)
