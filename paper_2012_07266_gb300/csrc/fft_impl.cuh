@@ -95,11 +95,42 @@ template <bool INV, typename C> __device__ __forceinline__ void dft3(C* v) {
   }
 }
 
+// 16 = 4 x 4: X[k1 + 4 k2] = sum_n1 W4^{n1 k2} W16^{n1 k1} sum_n2 W4^{n2 k1} x[n1 + 4 n2]
+template <bool INV, typename C> __device__ __forceinline__ void dft16(C* v) {
+  using R = decltype(C{}.x);
+  const R c1 = R(0.92387953251128675613), s1 = R(0.38268343236508977173);  // cos, sin pi/8
+  const R h = R(0.70710678118654752440);
+#pragma unroll
+  for (int n1 = 0; n1 < 4; ++n1) dft4<INV>(v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]);
+  // W16^m, m = n1 k1, for the forward sign; the inverse takes the conjugate
+  auto tw = [&](C& a, R wr, R wi) { a = cmul(a, C{wr, INV ? -wi : wi}); };
+  tw(v[5], c1, -s1);   // m = 1
+  tw(v[6], h, -h);     // m = 2
+  tw(v[7], s1, -c1);   // m = 3
+  tw(v[9], h, -h);     // m = 2
+  v[10] = mul_mi<INV>(v[10]);  // m = 4
+  tw(v[11], -h, -h);   // m = 6
+  tw(v[13], s1, -c1);  // m = 3
+  tw(v[14], -h, -h);   // m = 6
+  tw(v[15], -c1, s1);  // m = 9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose to natural order
+  C o[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) o[k1 + 4 * k2] = v[4 * k1 + k2];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = o[k];
+}
+
 template <int RAD, bool INV, typename C> __device__ __forceinline__ void dft(C* v) {
   if constexpr (RAD == 2) dft2<INV>(v);
   else if constexpr (RAD == 3) dft3<INV>(v);
   else if constexpr (RAD == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
-  else dft8<INV>(v);
+  else if constexpr (RAD == 8) dft8<INV>(v);
+  else dft16<INV>(v);
 }
 
 template <int... Rs> struct Radices {};
@@ -114,6 +145,11 @@ template <> struct Plan<192> { static constexpr int V = 24; using Rad = Radices<
 template <> struct Plan<256> { static constexpr int V = 8; using Rad = Radices<8, 8, 4>; };
 template <> struct Plan<512> { static constexpr int V = 8; using Rad = Radices<8, 8, 8>; };
 template <> struct Plan<1024> { static constexpr int V = 8; using Rad = Radices<8, 8, 8, 2>; };
+
+// Row FFTs of the x pass: 256 points in two radix-16 stages, one shared-memory
+// pass fewer than 8 x 8 x 4 and no stage whose stores fall 2-way on a bank
+template <int H> struct RowPlan : Plan<H> {};
+template <> struct RowPlan<256> { static constexpr int V = 16; using Rad = Radices<16, 16>; };
 
 // Element k of a unit-stride column sits at pad(k) = k + k / 16: the first
 // Stockham stage writes 8 consecutive outputs per thread (stride 8 across
@@ -222,17 +258,17 @@ __device__ __forceinline__ void run_stages(C* buf, int col, int t, const C* tw) 
     run_stages<C, N, V, INV, RS, CS, CP, NS * RAD, Rest...>(buf, col, t, NS > 1 ? tw + (RAD - 1) * NS : tw);
 }
 
-template <typename C, int N, bool INV, int RS, int CS, int CP, int... Rs>
+template <typename C, int N, int V, bool INV, int RS, int CS, int CP, int... Rs>
 __device__ __forceinline__ void fft_column_impl(Radices<Rs...>, C* buf, int col, int t, const C* tw) {
-  run_stages<C, N, Plan<N>::V, INV, RS, CS, CP, 1, Rs...>(buf, col, t, tw);
+  run_stages<C, N, V, INV, RS, CS, CP, 1, Rs...>(buf, col, t, tw);
 }
 
 // In-place FFT of CP adjacent columns of length N held in shared memory:
 // element k of column `col + c` at buf[k * RS + (col + c) * CS] (compile-time
-// strides).
-template <typename C, int N, bool INV, int RS, int CS, int CP = 1>
+// strides), with the radices and elements per thread of plan PL.
+template <typename C, int N, bool INV, int RS, int CS, int CP = 1, typename PL = Plan<N>>
 __device__ __forceinline__ void fft_column(C* buf, int col, int t, const C* tw) {
-  fft_column_impl<C, N, INV, RS, CS, CP>(typename Plan<N>::Rad{}, buf, col, t, tw);
+  fft_column_impl<C, N, PL::V, INV, RS, CS, CP>(typename PL::Rad{}, buf, col, t, tw);
 }
 
 // Stage-major twiddles of the plan of N: for each stage with NS > 1, in order,
@@ -260,8 +296,8 @@ __device__ __forceinline__ void fill_plan_twiddles(Radices<Rs...>, C* tw) {
   fill_stage_twiddles<C, 1, Rs...>(tw);
 }
 
-template <typename C, int N> __device__ __forceinline__ void make_twiddles(C* tw) {
-  fill_plan_twiddles<C>(typename Plan<N>::Rad{}, tw);
+template <typename C, int N, typename PL = Plan<N>> __device__ __forceinline__ void make_twiddles(C* tw) {
+  fill_plan_twiddles<C>(typename PL::Rad{}, tw);
 }
 
 // tu[k] = exp(-2 pi i k / N), k <= N / 2 (real <-> half-length complex untangling)
@@ -301,7 +337,8 @@ template <typename R, int N> struct ZTile {
 
 template <typename R, int N> struct RowTile {  // x pass: rows of N reals, FFT length N/2
   static constexpr int H = N / 2;
-  static constexpr int T = H / Plan<H>::V;
+  using PL = RowPlan<H>;
+  static constexpr int T = H / PL::V;
   static constexpr int ROWS = (256 / T) > 0 ? (256 / T) : 1;
   static constexpr int THREADS = ROWS * T;
 };
@@ -419,7 +456,7 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* tu = tw + H;        // untangle twiddles exp(-2 pi i k / N), k <= H
   C* buf = tu + H + 2;
-  make_twiddles<C, H>(tw);
+  make_twiddles<C, H, typename RowTile<R, N>::PL>(tw);
   make_untangle<C, N>(tu);
   const long long row0 = (long long)blockIdx.x * ROWS;
   {
@@ -453,7 +490,7 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   }
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
-  fft_column<C, H, false, 1, LD>(buf, h, t, tw);
+  fft_column<C, H, false, 1, LD, 1, typename RowTile<R, N>::PL>(buf, h, t, tw);
   // X[k] = (Z[k] + conj Z[H-k]) / 2 + e^{-2 pi i k / N} (Z[k] - conj Z[H-k]) / (2i), k <= H
   C* outb = out + row0 * P;
   auto untangle = [&](int hh, int k) {
@@ -479,7 +516,7 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + H + H + 2;
-  make_twiddles<C, H>(tw);
+  make_twiddles<C, H, typename RowTile<R, N>::PL>(tw);
   const long long row0 = (long long)blockIdx.x * ROWS;
   constexpr int THR = RowTile<R, N>::THREADS, PER = ROWS * H / THR;
   C vk[PER], vm[PER];
@@ -506,7 +543,7 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
   }
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
-  fft_column<C, H, true, 1, LD>(buf, h, t, tw);
+  fft_column<C, H, true, 1, LD, 1, typename RowTile<R, N>::PL>(buf, h, t, tw);
   C* outc = reinterpret_cast<C*>(out) + row0 * H;
   for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
     const int hh = e / H, m = e - hh * H;
