@@ -236,14 +236,21 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
 #pragma unroll
       for (int k = 0; k < RAD; ++k) wb[pad_step<NS, RAD, true, NS * RAD>(k)] = v[0][b][k];
     } else {
+      // first stage on 64-byte rows (8 FP32 columns): the lanes of consecutive t write rows
+      // RAD t + k, all on the same half of the banks; odd t write the butterfly's outputs in
+      // pair-swapped order (row k ^ 1), so that each store instruction covers every bank
+      constexpr bool SWAP = NS == 1 && RS != 1 && RS * (int)sizeof(C) == 64 && RAD % 2 == 0;
+      const int sw = SWAP ? (t & 1) : 0;
 #pragma unroll
       for (int k = 0; k < RAD; ++k) {
+        const int kk = k ^ sw;
         if constexpr (VEC) {
-          *reinterpret_cast<float4*>(&at(base + k * NS, 0)) =
-              make_float4(v[0][b][k].x, v[0][b][k].y, v[CP - 1][b][k].x, v[CP - 1][b][k].y);
+          const C a = SWAP && sw ? v[0][b][k ^ 1] : v[0][b][k];
+          const C c = SWAP && sw ? v[CP - 1][b][k ^ 1] : v[CP - 1][b][k];
+          *reinterpret_cast<float4*>(&at(base + kk * NS, 0)) = make_float4(a.x, a.y, c.x, c.y);
         } else {
 #pragma unroll
-          for (int cc = 0; cc < CP; ++cc) at(base + k * NS, cc) = v[cc][b][k];
+          for (int cc = 0; cc < CP; ++cc) at(base + kk * NS, cc) = SWAP && sw ? v[cc][b][k ^ 1] : v[cc][b][k];
         }
       }
     }
