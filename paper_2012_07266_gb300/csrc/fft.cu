@@ -16,7 +16,7 @@ struct Launch {
   static constexpr double RB = (double)N * N * N * sizeof(R);
   static constexpr double CB = (double)N * N * (N / 2 + 1) * sizeof(C);
   static size_t smem_x() {
-    return (size_t)(N / 2 + N / 2 + 2 + RowTile<R, N>::ROWS * (PadLen<N / 2>::value + 1)) * sizeof(C);
+    return (size_t)RowTile<R, N>::SMEM;
   }
   static size_t smem_cols() { return (size_t)(N + N * ColTile<R, N>::W) * sizeof(C); }
   static size_t smem_z() { return (size_t)(N + 2 * N * ZTile<R, N>::W) * sizeof(C); }

@@ -348,6 +348,8 @@ template <typename R, int N> struct RowTile {  // x pass: rows of N reals, FFT l
   static constexpr int T = H / PL::V;
   static constexpr int ROWS = (256 / T) > 0 ? (256 / T) : 1;
   static constexpr int THREADS = ROWS * T;
+  // twiddles, untangle table and the padded rows
+  static constexpr int SMEM = (H + H + 2 + ROWS * (PadLen<H>::value + 1)) * 2 * (int)sizeof(R);
 };
 
 // ------------------------------------------------------------ tile copies
@@ -525,28 +527,61 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
   C* buf = tw + H + H + 2;
   make_twiddles<C, H, typename RowTile<R, N>::PL>(tw);
   const long long row0 = (long long)blockIdx.x * ROWS;
-  constexpr int THR = RowTile<R, N>::THREADS, PER = ROWS * H / THR;
-  C vk[PER], vm[PER];
+  constexpr int THR = RowTile<R, N>::THREADS;
   const C* inb = in + row0 * P;  // 32-bit offsets within the block's rows
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int e = threadIdx.x + q * THR;
-    const int h = e / H, k = e - h * H;
-    vk[q] = inb[h * P + k];
-    vm[q] = inb[h * P + (H - k)];
-  }
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int e = threadIdx.x + q * THR;
-    const int h = e / H, k = e - h * H;
-    const C xk = vk[q];
-    const C xm = cconj(vm[q]);
-    const C ev = cadd(xk, xm);
+  // Z[k] = (X[k] + conj X[H-k]) + i w_k (X[k] - conj X[H-k]), w_k = exp(2 pi i k / N)
+  auto untangle = [](C a, C b, C w) {
+    const C bm = cconj(b);
+    const C ev = cadd(a, bm);
+    const C od = cmul(w, csub(a, bm));
+    return C{ev.x - od.y, ev.y + od.x};  // ev + i od
+  };
+  auto untwiddle = [](int k) {
     R s, c;
     if constexpr (sizeof(R) == 4) sincospif(2.0f * (float)k / (float)N, &s, &c);
     else sincospi(2.0 * (double)k / (double)N, &s, &c);
-    const C od = cmul(C{c, s}, csub(xk, xm));
-    buf[h * LD + pad16(k)] = C{ev.x - od.y, ev.y + od.x};  // ev + i od
+    return C{c, s};
+  };
+  if constexpr (THR % (H / 2) == 0) {
+    // every input read once: the thread of pair k < H/2 reads X[k] and X[H - k] and writes
+    // Z[k] and Z[H - k] (w_{H-k} = -conj w_k); the thread of pair 0 also makes Z[H/2]
+    constexpr int PER = ROWS * (H / 2) / THR;
+    const int k = threadIdx.x % (H / 2);
+    C xa[PER], xb[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int h = (threadIdx.x + q * THR) / (H / 2);
+      xa[q] = inb[h * P + k];
+      xb[q] = inb[h * P + (H - k)];
+    }
+    const C w = untwiddle(k), wm = C{-w.x, w.y};
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int h = (threadIdx.x + q * THR) / (H / 2);
+      buf[h * LD + pad16(k)] = untangle(xa[q], xb[q], w);
+      if (k > 0) {
+        buf[h * LD + pad16(H - k)] = untangle(xb[q], xa[q], wm);
+      } else {
+        const C c = inb[h * P + H / 2];
+        buf[h * LD + pad16(H / 2)] = untangle(c, c, C{R(0), R(1)});
+      }
+    }
+  } else {
+    constexpr int PER = ROWS * H / THR;
+    C vk[PER], vm[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * THR;
+      const int h = e / H, k = e - h * H;
+      vk[q] = inb[h * P + k];
+      vm[q] = inb[h * P + (H - k)];
+    }
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int e = threadIdx.x + q * THR;
+      const int h = e / H, k = e - h * H;
+      buf[h * LD + pad16(k)] = untangle(vk[q], vm[q], untwiddle(k));
+    }
   }
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
