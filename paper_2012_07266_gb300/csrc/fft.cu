@@ -35,6 +35,20 @@ struct Launch {
     return std::min(tiles, slots);
   }
 
+  // persistent x c2r: every block slot the occupancy allows
+  static int x_grid(int nblk) {
+    static const int slots = [] {
+      attrs();
+      int per_sm = 0, dev = 0, nsm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_x_c2r<R, N>, RowTile<R, N>::THREADS,
+                                                    smem_x());
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      return std::max(per_sm, 1) * std::max(nsm, 1);
+    }();
+    return std::min(nblk, slots);
+  }
+
   static void attrs() {
     static bool done = false;
     if (done) return;
@@ -60,7 +74,8 @@ struct Launch {
   }
   static void x_inv(const C* in, R* out, int P, cudaStream_t s, Prof* pf, int kind) {
     ProfScope ps(pf, kind >= 0 ? kind : KK_FFT_X_INV, s, RB + CB);
-    k_fft_x_c2r<R, N><<<(long long)N * N / RowTile<R, N>::ROWS, RowTile<R, N>::THREADS, smem_x(), s>>>(in, out, P);
+    const int nblk = N * N / RowTile<R, N>::ROWS;
+    k_fft_x_c2r<R, N><<<x_grid(nblk), RowTile<R, N>::THREADS, smem_x(), s>>>(in, out, P, nblk);
   }
   // column pass over all N planes through the TMA pipeline (err != null) or
   // the plain tile kernel

@@ -516,19 +516,20 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   for (int hh = threadIdx.x; hh < ROWS; hh += blockDim.x) untangle(hh, H);
 }
 
-// x pass, inverse: half-spectrum rows -> real rows (unnormalised: n * IDFT)
+// x pass, inverse: half-spectrum rows -> real rows (unnormalised: n * IDFT).
+// Persistent over blocks of ROWS rows: with pair loads, the next block's input is
+// requested right after the current one has been untangled into shared memory,
+// so that its HBM latency overlaps the shared-memory FFT.
 template <typename R, int N>
 __global__ void __launch_bounds__(RowTile<R, N>::THREADS)
-k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P) {
+k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P, int nblk) {
   using C = typename CT<R>::T;
   constexpr int H = N / 2, ROWS = RowTile<R, N>::ROWS, T = RowTile<R, N>::T, LD = PadLen<H>::value + 1;
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* buf = tw + H + H + 2;
   make_twiddles<C, H, typename RowTile<R, N>::PL>(tw);
-  const long long row0 = (long long)blockIdx.x * ROWS;
   constexpr int THR = RowTile<R, N>::THREADS;
-  const C* inb = in + row0 * P;  // 32-bit offsets within the block's rows
   // Z[k] = (X[k] + conj X[H-k]) + i w_k (X[k] - conj X[H-k]), w_k = exp(2 pi i k / N)
   auto untangle = [](C a, C b, C w) {
     const C bm = cconj(b);
@@ -542,54 +543,67 @@ k_fft_x_c2r(const typename CT<R>::T* __restrict__ in, R* __restrict__ out, int P
     else sincospi(2.0 * (double)k / (double)N, &s, &c);
     return C{c, s};
   };
+  const int h = threadIdx.x / T, t = threadIdx.x - h * T;
+  auto transform_store = [&](int blk) {
+    __syncthreads();
+    fft_column<C, H, true, 1, LD, 1, typename RowTile<R, N>::PL>(buf, h, t, tw);
+    C* outc = reinterpret_cast<C*>(out) + (long long)blk * ROWS * H;
+    for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
+      const int hh = e / H, m = e - hh * H;
+      outc[e] = buf[hh * LD + pad16(m)];
+    }
+    __syncthreads();  // buf is refilled by the next block's untangling
+  };
   if constexpr (THR % (H / 2) == 0) {
     // every input read once: the thread of pair k < H/2 reads X[k] and X[H - k] and writes
-    // Z[k] and Z[H - k] (w_{H-k} = -conj w_k); the thread of pair 0 also makes Z[H/2]
+    // Z[k] and Z[H - k] (w_{H-k} = -conj w_k); the thread of pair 0 also reads X[H/2]
     constexpr int PER = ROWS * (H / 2) / THR;
     const int k = threadIdx.x % (H / 2);
-    C xa[PER], xb[PER];
+    C xa[PER], xb[PER], xc[PER];
+    auto load = [&](int blk) {
+      const C* inb = in + (long long)blk * ROWS * P;  // 32-bit offsets within the block's rows
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int h = (threadIdx.x + q * THR) / (H / 2);
-      xa[q] = inb[h * P + k];
-      xb[q] = inb[h * P + (H - k)];
-    }
-    const C w = untwiddle(k), wm = C{-w.x, w.y};
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int h = (threadIdx.x + q * THR) / (H / 2);
-      buf[h * LD + pad16(k)] = untangle(xa[q], xb[q], w);
-      if (k > 0) {
-        buf[h * LD + pad16(H - k)] = untangle(xb[q], xa[q], wm);
-      } else {
-        const C c = inb[h * P + H / 2];
-        buf[h * LD + pad16(H / 2)] = untangle(c, c, C{R(0), R(1)});
+      for (int q = 0; q < PER; ++q) {
+        const int hq = (threadIdx.x + q * THR) / (H / 2);
+        xa[q] = inb[hq * P + k];
+        xb[q] = inb[hq * P + (H - k)];
+        if (k == 0) xc[q] = inb[hq * P + H / 2];
       }
+    };
+    const C w = untwiddle(k), wm = C{-w.x, w.y};
+    int blk = blockIdx.x;
+    if (blk < nblk) load(blk);
+    for (; blk < nblk; blk += gridDim.x) {
+#pragma unroll
+      for (int q = 0; q < PER; ++q) {
+        const int hq = (threadIdx.x + q * THR) / (H / 2);
+        buf[hq * LD + pad16(k)] = untangle(xa[q], xb[q], w);
+        if (k > 0) buf[hq * LD + pad16(H - k)] = untangle(xb[q], xa[q], wm);
+        else buf[hq * LD + pad16(H / 2)] = untangle(xc[q], xc[q], C{R(0), R(1)});
+      }
+      if (blk + (int)gridDim.x < nblk) load(blk + gridDim.x);
+      transform_store(blk);
     }
   } else {
     constexpr int PER = ROWS * H / THR;
-    C vk[PER], vm[PER];
+    for (int blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
+      const C* inb = in + (long long)blk * ROWS * P;
+      C vk[PER], vm[PER];
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = threadIdx.x + q * THR;
-      const int h = e / H, k = e - h * H;
-      vk[q] = inb[h * P + k];
-      vm[q] = inb[h * P + (H - k)];
-    }
+      for (int q = 0; q < PER; ++q) {
+        const int e = threadIdx.x + q * THR;
+        const int hq = e / H, k = e - hq * H;
+        vk[q] = inb[hq * P + k];
+        vm[q] = inb[hq * P + (H - k)];
+      }
 #pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int e = threadIdx.x + q * THR;
-      const int h = e / H, k = e - h * H;
-      buf[h * LD + pad16(k)] = untangle(vk[q], vm[q], untwiddle(k));
+      for (int q = 0; q < PER; ++q) {
+        const int e = threadIdx.x + q * THR;
+        const int hq = e / H, k = e - hq * H;
+        buf[hq * LD + pad16(k)] = untangle(vk[q], vm[q], untwiddle(k));
+      }
+      transform_store(blk);
     }
-  }
-  __syncthreads();
-  const int h = threadIdx.x / T, t = threadIdx.x - h * T;
-  fft_column<C, H, true, 1, LD, 1, typename RowTile<R, N>::PL>(buf, h, t, tw);
-  C* outc = reinterpret_cast<C*>(out) + row0 * H;
-  for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
-    const int hh = e / H, m = e - hh * H;
-    outc[e] = buf[hh * LD + pad16(m)];
   }
 }
 
