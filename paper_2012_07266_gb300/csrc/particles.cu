@@ -136,14 +136,15 @@ template <typename R>
 __global__ void __launch_bounds__(256) k_kdk_paint(PState<R> s, const R* __restrict__ F0, const R* __restrict__ F1,
                                                    const R* __restrict__ F2, R* __restrict__ rho, int M, R ckick,
                                                    R cdrift, R mass, long long np) {
-  // two independent particles per iteration: their gathers and reductions overlap
-  const long long S = (long long)gridDim.x * blockDim.x;
-  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  for (; j + S < np; j += 2 * S) {
+  // each block walks one contiguous run of the (spatially sorted) particles, so that the mesh
+  // rows its gathers and reductions touch are reused while they are in L2; two independent
+  // particles per thread and iteration (adjacent lines): their gathers and reductions overlap
+  const long long per = (np + gridDim.x - 1) / gridDim.x;
+  const long long j0 = blockIdx.x * per, j1 = j0 + per < np ? j0 + per : np;
+  for (long long j = j0 + threadIdx.x; j < j1; j += 2 * (long long)blockDim.x) {
     kdk_one(s, F0, F1, F2, rho, M, ckick, cdrift, mass, j);
-    kdk_one(s, F0, F1, F2, rho, M, ckick, cdrift, mass, j + S);
+    if (j + blockDim.x < j1) kdk_one(s, F0, F1, F2, rho, M, ckick, cdrift, mass, j + blockDim.x);
   }
-  if (j < np) kdk_one(s, F0, F1, F2, rho, M, ckick, cdrift, mass, j);
 }
 
 // readout at the particles, written in lattice order (out[pid[j]])
