@@ -59,3 +59,35 @@ def test_config_validation_returns_errors_before_device_work(L):
     assert so.pm_strerror(5) == b"entry point called out of order"
     assert so.pm_strerror(7) == b"device-side wait for a bulk copy timed out"
     assert L.STATUS[7] == "PM_ERR_TIMEOUT"
+
+
+def test_map_cl_host_validation(L):
+    """pm_map_cl and its workspace query refuse bad sizes, edges and workspaces before any
+    device work (the device pointers below are never dereferenced)."""
+    so = L.load()
+    n = C.c_size_t(0)
+    assert so.pm_map_cl_workspace_size(64, 2, 8, C.byref(n)) == 0
+    # work (64^2 complex) + twiddles + edges + sums + counts, each 256-byte aligned
+    expect = sum(-(-b // 256) * 256 for b in (64 * 64 * 16, 32 * 16, 9 * 8, 2 * 8 * 8, 8 * 8))
+    assert n.value == expect
+    for args in [(48, 1, 4), (4, 1, 4), (8192, 1, 4), (64, 0, 4), (64, 1, 0), (64, 1, 2049)]:
+        assert so.pm_map_cl_workspace_size(*args, C.byref(n)) == 1, args
+    assert so.pm_map_cl_workspace_size(64, 1, 4, None) == 1
+    fake = C.c_void_p(0x1000)
+
+    def call(edges, npix=64, nmaps=1, fov=2.0, alpha=1.0, beta=0.0, ws=fake, nbytes=1 << 20, out=fake):
+        e = (C.c_double * len(edges))(*edges)
+        return so.pm_map_cl(fake, nmaps, npix, fov, C.cast(e, C.c_void_p), len(edges) - 1, alpha, beta, out,
+                            None, ws, nbytes, None)
+    good = [0.0, 1.0, 2.0, float("inf")]
+    assert call(good, npix=96) == 1                       # not a power of two
+    assert call([0.0, 2.0, 1.0]) == 1                     # not ascending
+    assert call([0.0, 1.0, 1.0]) == 1                     # repeated edge
+    assert call([0.0, float("nan"), 2.0]) == 1
+    assert call(good, fov=-1.0) == 1
+    assert call(good, alpha=float("inf")) == 1
+    assert call(good, out=None) == 1
+    assert call(good, ws=None) == 1
+    assert call(good, nbytes=1024) == 2                   # workspace too small
+    assert call(good, ws=C.c_void_p(0x1010)) == 2         # workspace not 256-byte aligned
+    assert so.pm_shot_noise_maps(None, 1, fake) == 1

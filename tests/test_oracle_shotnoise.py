@@ -134,3 +134,32 @@ def test_shot_noise_map_mean():
     assert abs(m - (J - 1) * mean_term) < 4 * sd
     # the mean term matters: without it the mean is off by many deviations
     assert mean_term > 20 * sd
+
+
+def test_cl_against_direct_sum():
+    """The estimator against its definition written out on a tiny map: kappa~(l) =
+    Omega_pix sum_j kappa_j exp(-i l . theta_j) over the pixel-centre angles theta_j,
+    C(l) = |kappa~(l)|^2 / Omega_map, at l = (2 pi / FOV) m; bins one |m| shell wide."""
+    rng = np.random.default_rng(5)
+    n, fov = 8, 1.5
+    kappa = rng.standard_normal((n, n))
+    fr = np.deg2rad(fov)
+    dth = fr / n
+    th = (np.arange(n) + 0.5) * dth - 0.5 * fr
+    lscale = 2 * np.pi / fr
+    k2s = sorted({mx * mx + my * my for mx in range(-n // 2, n // 2) for my in range(-n // 2, n // 2)})
+    edges = [lscale * (np.sqrt(k) - 1e-9) for k in k2s] + [lscale * n]
+    sums, cnt = np.zeros(len(k2s)), np.zeros(len(k2s))
+    for mx in range(-n // 2, n // 2):
+        for my in range(-n // 2, n // 2):
+            acc = 0j
+            for iy in range(n):
+                for ix in range(n):
+                    acc += kappa[iy, ix] * np.exp(-1j * lscale * (mx * th[ix] + my * th[iy]))
+            c = abs(acc * dth * dth) ** 2 / fr ** 2
+            b = k2s.index(mx * mx + my * my)
+            sums[b] += c
+            cnt[b] += 1
+    cl, counts = angular_cl(kappa, fov, edges)
+    assert list(counts) == list(cnt.astype(int))
+    assert np.allclose(cl, sums / cnt, rtol=1e-11, atol=0)
