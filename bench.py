@@ -176,6 +176,28 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# -------------------------------------------------- ranks (replicas only)
+def rank_noise_seed(w, rank):
+    """Every rank runs its own independent simulation (ensemble sharding): rank r draws the
+    white noise of seed noise_seed + r; nothing is exchanged on the data path."""
+    return w["noise_seed"] + rank
+
+
+def max_over_ranks(x, dist=None, device=None):
+    """The slowest rank's time: an all-reduce MAX of one number (no-op on one rank)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world, npart, nsteps, ms):
+    """Whole-job particle-steps per second: all ranks' particle steps over the slowest rank's time."""
+    return world * npart * nsteps / (ms * 1e-3)
+
+
 # ------------------------------------------------------------- GPU arm
 def run_gpu(a, rank, world, local_rank):
     import torch
@@ -199,7 +221,7 @@ def run_gpu(a, rank, world, local_rank):
     prec = PM_FP64 if a.precision == "fp64" else PM_FP32
     stream = torch.cuda.Stream(dev)
     sim = Simulation(device=dev, stream=stream, precision=prec, **w)
-    noise = torch.from_numpy(white_noise(w["nc"], w["noise_seed"] + rank)).to(dev)
+    noise = torch.from_numpy(white_noise(w["nc"], rank_noise_seed(w, rank))).to(dev)
     npart, nsteps = w["nc"] ** 3, w["nsteps"]
 
     def one():
@@ -222,18 +244,14 @@ def run_gpu(a, rank, world, local_rank):
     clk = clocks.stop()
     sim.profile(False)
     prof = sim.profile_read()
-    ms = ev0.elapsed_time(ev1) / a.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * npart * nsteps / (ms * 1e-3)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / a.steps, dist, dev)
+    value = aggregate_rate(world, npart, nsteps, ms)
     launches = sum(v[1] for v in prof.values())
 
     # end to end through the public API with host buffers (pinned)
     e2e = None
     if not a.no_e2e:
-        h_noise = torch.from_numpy(white_noise(w["nc"], w["noise_seed"] + rank)).pin_memory()
+        h_noise = torch.from_numpy(white_noise(w["nc"], rank_noise_seed(w, rank))).pin_memory()
         h_kappa = torch.empty((sim.n_zs, sim.npix, sim.npix), dtype=torch.float64).pin_memory()
         d_noise = torch.empty_like(h_noise, device=dev)
         d_kappa = torch.empty((sim.n_zs, sim.npix, sim.npix), dtype=torch.float64, device=dev)
@@ -258,12 +276,8 @@ def run_gpu(a, rank, world, local_rank):
         e1.record(stream)
         e1.synchronize()
         barrier()
-        ems = e0.elapsed_time(e1) / a.steps
-        if dist is not None:
-            t = torch.tensor([ems], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        e2e = {"value": world * npart * nsteps / (ems * 1e-3), "unit": UNIT,
+        ems = max_over_ranks(e0.elapsed_time(e1) / a.steps, dist, dev)
+        e2e = {"value": aggregate_rate(world, npart, nsteps, ems), "unit": UNIT,
                "h2d_bytes_per_step": h_noise.numel() * 8, "d2h_bytes_per_step": h_kappa.numel() * 8}
 
     if rank != 0:
@@ -331,7 +345,7 @@ def extra_legs(a, w, dev, rank):
     from pm_inputs import serving_arrivals, white_noise, workload
     out = {}
     npart, nsteps = w["nc"] ** 3, w["nsteps"]
-    noise = torch.from_numpy(white_noise(w["nc"], w["noise_seed"] + rank)).to(dev)
+    noise = torch.from_numpy(white_noise(w["nc"], rank_noise_seed(w, rank))).to(dev)
     # forward + reverse-mode derivative: resident (every step's state and meshes kept in HBM,
     # no recompute) and checkpointed every 4 steps (one recompute of each segment)
     stream = torch.cuda.Stream(dev)
