@@ -25,6 +25,8 @@ def map_cl(maps: torch.Tensor, fov_deg: float, edges, alpha=1.0, beta=0.0, out=N
     """Binned flat-sky angular power spectrum of maps (..., npix, npix) on their
     GPU (pm_map_cl): out = beta * out + alpha * C(l) per map and bin; with
     return_counts also the number of modes per bin."""
+    if not maps.is_cuda or maps.dim() < 2 or maps.shape[-1] != maps.shape[-2]:
+        raise ValueError("map_cl: maps must be a CUDA tensor of shape (..., npix, npix)")
     maps = maps.to(dtype=torch.float64).contiguous()
     npix = int(maps.shape[-1])
     nmaps = maps.numel() // (npix * npix)
@@ -37,6 +39,9 @@ def map_cl(maps: torch.Tensor, fov_deg: float, edges, alpha=1.0, beta=0.0, out=N
     ws.record_stream(stream)
     if out is None:
         out = torch.zeros(tuple(maps.shape[:-2]) + (nb,), dtype=torch.float64, device=maps.device)
+    elif (out.device != maps.device or out.dtype != torch.float64 or not out.is_contiguous()
+          or out.numel() != nmaps * nb):
+        raise ValueError("map_cl: out must be a contiguous float64 tensor of nmaps x nbins on the maps' device")
     eh = (C.c_double * (nb + 1))(*edges)
     counts = (C.c_int64 * nb)() if return_counts else None
     lib.call("pm_map_cl", _ptr(maps), nmaps, npix, float(fov_deg), C.cast(eh, C.c_void_p), nb, float(alpha),
@@ -106,6 +111,9 @@ class Simulation:
     def kappa_maps(self, out: torch.Tensor | None = None) -> torch.Tensor:
         if out is None:
             out = self._f64(self.n_zs, self.npix, self.npix)
+        elif (not out.is_cuda or out.dtype != torch.float64 or not out.is_contiguous()
+              or out.numel() != self.n_zs * self.npix * self.npix):
+            raise ValueError("kappa_maps: out must be a contiguous float64 (n_zs, npix, npix) tensor on the device")
         lib.call("kappa_maps", self.ctx, _ptr(out))
         return out
 
