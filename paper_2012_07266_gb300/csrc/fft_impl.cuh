@@ -16,10 +16,12 @@
 //    gradient, PGD filter, LPT operators), inverse z FFT, store -- the
 //    spectrum itself never goes back to HBM.
 //
-// The 1D transform is a mixed-radix (8, 4, 2, 3) Stockham auto-sort FFT: each
-// stage reads the r inputs of a butterfly at stride n/r, applies twiddles
-// W_{Ns r}^{(j mod Ns) k}, a radix-r DFT in registers, and writes to
-// (j div Ns) Ns r + (j mod Ns) + k Ns, leaving the output in natural order.
+// The 1D transform is a mixed-radix (16, 8, 4, 2, 3) Stockham auto-sort FFT:
+// each stage reads the r inputs of a butterfly at stride n/r, applies twiddles
+// W_{Ns r}^{(j mod Ns) k} (from a stage-major table, so that the consecutive
+// butterflies of a warp read consecutive entries), a radix-r DFT in registers,
+// and writes to (j div Ns) Ns r + (j mod Ns) + k Ns, leaving the output in
+// natural order.
 #pragma once
 
 #include <cuda_runtime.h>
