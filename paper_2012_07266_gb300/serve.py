@@ -76,18 +76,23 @@ class Server:
         self._used = 0
         self._active = 0
 
+    def _execute(self, req: Request):
+        """The request's device work on its own stream: the forward run, and the
+        reverse sweep when the request asks for gradients."""
+        stream = torch.cuda.Stream(self.device)
+        with torch.cuda.stream(stream):
+            sim = Simulation(device=self.device, stream=stream, precision=self.precision, **req.params)
+            noise = torch.from_numpy(req.noise).to(self.device, non_blocking=False)
+            req.kappa = sim.run(noise)  # kappa_maps synchronises this request's stream
+            if req.adjoint:
+                # gradient of L = sum(kappa^2) / 2
+                req.grad_noise, req.grad_params = sim.vjp(req.kappa)
+            stream.synchronize()
+            del sim
+
     def _run_one(self, req: Request, nbytes: int, t0: float, stats: ServeStats):
         try:
-            stream = torch.cuda.Stream(self.device)
-            with torch.cuda.stream(stream):
-                sim = Simulation(device=self.device, stream=stream, precision=self.precision, **req.params)
-                noise = torch.from_numpy(req.noise).to(self.device, non_blocking=False)
-                req.kappa = sim.run(noise)  # kappa_maps synchronises this request's stream
-                if req.adjoint:
-                    # gradient of L = sum(kappa^2) / 2
-                    req.grad_noise, req.grad_params = sim.vjp(req.kappa)
-                stream.synchronize()
-                del sim
+            self._execute(req)
         except Exception as e:  # the request fails, the server keeps serving
             req.error = repr(e)
         req.t_done = time.perf_counter() - t0
