@@ -24,29 +24,34 @@ def map_cl(maps: torch.Tensor, fov_deg: float, edges, alpha=1.0, beta=0.0, out=N
            return_counts=False):
     """Binned flat-sky angular power spectrum of maps (..., npix, npix) on their
     GPU (pm_map_cl): out = beta * out + alpha * C(l) per map and bin; with
-    return_counts also the number of modes per bin."""
+    return_counts also the number of modes per bin.  Every device step (a float64
+    copy of the maps when one is needed, the workspace, the output) is ordered on
+    `stream` (default: the current stream), on which the maps must be ready."""
     if not maps.is_cuda or maps.dim() < 2 or maps.shape[-1] != maps.shape[-2]:
         raise ValueError("map_cl: maps must be a CUDA tensor of shape (..., npix, npix)")
-    maps = maps.to(dtype=torch.float64).contiguous()
-    npix = int(maps.shape[-1])
-    nmaps = maps.numel() // (npix * npix)
-    edges = [float(e) for e in edges]
-    nb = len(edges) - 1
-    n = C.c_size_t(0)
-    lib.call("pm_map_cl_workspace_size", npix, nmaps, nb, C.byref(n))
+    if out is None and beta != 0.0:
+        raise ValueError("map_cl: beta != 0 accumulates into out, which must then be given")
     stream = stream if stream is not None else torch.cuda.current_stream(maps.device)
-    ws = torch.empty(int(n.value), dtype=torch.uint8, device=maps.device)
-    ws.record_stream(stream)
-    if out is None:
-        out = torch.zeros(tuple(maps.shape[:-2]) + (nb,), dtype=torch.float64, device=maps.device)
-    elif (out.device != maps.device or out.dtype != torch.float64 or not out.is_contiguous()
-          or out.numel() != nmaps * nb):
-        raise ValueError("map_cl: out must be a contiguous float64 tensor of nmaps x nbins on the maps' device")
-    eh = (C.c_double * (nb + 1))(*edges)
-    counts = (C.c_int64 * nb)() if return_counts else None
-    lib.call("pm_map_cl", _ptr(maps), nmaps, npix, float(fov_deg), C.cast(eh, C.c_void_p), nb, float(alpha),
-             float(beta), _ptr(out), C.cast(counts, C.c_void_p) if counts is not None else None, _ptr(ws),
-             C.c_size_t(n.value), C.c_void_p(stream.cuda_stream))
+    with torch.cuda.stream(stream):
+        maps = maps.to(dtype=torch.float64).contiguous()
+        npix = int(maps.shape[-1])
+        nmaps = maps.numel() // (npix * npix)
+        edges = [float(e) for e in edges]
+        nb = len(edges) - 1
+        n = C.c_size_t(0)
+        lib.call("pm_map_cl_workspace_size", npix, nmaps, nb, C.byref(n))
+        ws = torch.empty(int(n.value), dtype=torch.uint8, device=maps.device)
+        if out is None:
+            # beta = 0: the library writes every entry
+            out = torch.empty(tuple(maps.shape[:-2]) + (nb,), dtype=torch.float64, device=maps.device)
+        elif (out.device != maps.device or out.dtype != torch.float64 or not out.is_contiguous()
+              or out.numel() != nmaps * nb):
+            raise ValueError("map_cl: out must be a contiguous float64 tensor of nmaps x nbins on the maps' device")
+        eh = (C.c_double * (nb + 1))(*edges)
+        counts = (C.c_int64 * nb)() if return_counts else None
+        lib.call("pm_map_cl", _ptr(maps), nmaps, npix, float(fov_deg), C.cast(eh, C.c_void_p), nb, float(alpha),
+                 float(beta), _ptr(out), C.cast(counts, C.c_void_p) if counts is not None else None, _ptr(ws),
+                 C.c_size_t(n.value), C.c_void_p(stream.cuda_stream))
     return (out, [int(v) for v in counts]) if return_counts else out
 
 
@@ -96,9 +101,15 @@ class Simulation:
     def _f64(self, *shape):
         return torch.empty(*shape, dtype=torch.float64, device=self.device)
 
+    def _in64(self, t: torch.Tensor) -> torch.Tensor:
+        """t as a contiguous float64 tensor on the device; a conversion, when one is
+        needed, runs on this simulation's stream, ahead of the library's use of it."""
+        with torch.cuda.stream(self.stream):
+            return t.to(device=self.device, dtype=torch.float64).contiguous()
+
     # -- the method's entry points
     def ic(self, noise: torch.Tensor):
-        noise = noise.to(device=self.device, dtype=torch.float64).contiguous()
+        noise = self._in64(noise)
         self._noise = noise  # kept alive until the stream has consumed it
         lib.call("pm_ic", self.ctx, _ptr(noise))
 
@@ -127,8 +138,8 @@ class Simulation:
     def jvp(self, noise: torch.Tensor, dnoise: torch.Tensor):
         """(kappa, dkappa): a whole forward run from `noise` and the derivative of
         the maps along the noise direction `dnoise` (needs jvp=1 in the workload)."""
-        noise = noise.to(device=self.device, dtype=torch.float64).contiguous()
-        dnoise = dnoise.to(device=self.device, dtype=torch.float64).contiguous()
+        noise = self._in64(noise)
+        dnoise = self._in64(dnoise)
         self._noise = (noise, dnoise)  # kept alive until the stream has consumed them
         kappa = self._f64(self.n_zs, self.npix, self.npix)
         dkappa = self._f64(self.n_zs, self.npix, self.npix)
@@ -136,7 +147,7 @@ class Simulation:
         return kappa, dkappa
 
     def vjp(self, dL_dkappa: torch.Tensor, want_noise=True):
-        g = dL_dkappa.to(device=self.device, dtype=torch.float64).contiguous()
+        g = self._in64(dL_dkappa)
         dn = self._f64(self.nc, self.nc, self.nc) if want_noise else None
         hp = (C.c_double * 2)()
         lib.call("pm_vjp", self.ctx, _ptr(g), _ptr(dn), C.cast(hp, C.c_void_p))
@@ -179,8 +190,8 @@ class Simulation:
         return x, p
 
     def set_particles(self, x: torch.Tensor, p: torch.Tensor, next_step: int):
-        x = x.to(device=self.device, dtype=torch.float64).contiguous()
-        p = p.to(device=self.device, dtype=torch.float64).contiguous()
+        x = self._in64(x)
+        p = self._in64(p)
         self._keep = (x, p)
         lib.call("pm_set_particles", self.ctx, _ptr(x), _ptr(p), int(next_step))
 
@@ -202,7 +213,7 @@ class Simulation:
 
     def fft_r2c(self, field: torch.Tensor) -> torch.Tensor:
         m = self.cfg.nmesh
-        f = field.to(device=self.device, dtype=torch.float64).contiguous()
+        f = self._in64(field)
         out = self._f64(m, m, m // 2 + 1, 2)
         lib.call("pm_fft_r2c", self.ctx, _ptr(f), _ptr(out))
         return torch.view_as_complex(out)
