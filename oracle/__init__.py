@@ -21,6 +21,11 @@ quadrature, ODE integration, interpolation), following the paper's method:
   the flat-sky angular power spectrum of the maps (``shotnoise``)
 
 Readings of points the paper leaves open are stated in each function's
-docstring.  Parity unpinned: absolute Eisenstein-Hu transfer values (only
-limits and the sound-horizon fit pin them).
+docstring.  The Eisenstein-Hu transfer function is pinned through its CDM part
+(the Omega_b -> 0 limit against EH98's separately published zero-baryon fit, 1.5%)
+and its averaged baryon suppression (the no-wiggle fit, 2%) and sound horizon;
+the sigma_8 normalisation through the top-hat window's series and exact values
+and the closed-form variance of power laws.  Parity unpinned: the amplitude of
+the baryon wiggles (the constants of alpha_b, beta_node, beta_b and k_silk),
+which no independent formula in reach fixes.
 """
