@@ -23,6 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 from .cosmology import C_OVER_H0, Cosmology
+from . import dft
 from .lightcone import LensGeometry, apply_rotation, apply_transform, candidate_replicas, replica_transform
 from .lpt import linear_modes, lpt_displacements, lpt_state
 from .mesh import (cic_paint, cic_readout, cic_readout_grad, force_mesh, gradient_multipliers,
@@ -36,8 +37,8 @@ def _odd_op(mesh_list, multipliers):
     shape = mesh_list[0].shape
     acc = 0
     for m, mult in zip(mesh_list, multipliers):
-        acc = acc + mult * np.fft.rfftn(m)
-    return np.fft.irfftn(acc, s=shape, axes=(0, 1, 2))
+        acc = acc + mult * dft.rfftn(m)
+    return dft.irfftn(acc, s=shape, axes=(0, 1, 2))
 
 
 def mesh_force_vjp(x, v, nc, nmesh, box, kernel_meshes, kernel_mults):
@@ -197,7 +198,7 @@ def lpt_vjp(lam_psi1, lam_psi2, delta_k, nc, box, cosmo, order):
     # Psi1_j = IDFT[m_j amp DFT(w)], odd -> transpose is minus itself
     acc = 0
     for j in range(3):
-        acc = acc - mult[j] * amp * np.fft.rfftn(lam_psi1[:, j].reshape(shape))
+        acc = acc - mult[j] * amp * dft.rfftn(lam_psi1[:, j].reshape(shape))
     if order == 2 and lam_psi2 is not None:
         kk = (kx, ky, kz)
         kny = np.pi * nc / box
@@ -211,16 +212,16 @@ def lpt_vjp(lam_psi1, lam_psi2, delta_k, nc, box, cosmo, order):
             for b in range(a, 3):
                 mab = -(kk[a] * kk[a] if a == b else odd[a] * odd[b]) * inv
                 mults[(a, b)] = mab
-                d[(a, b)] = np.fft.irfftn(mab * delta_k, s=shape, axes=(0, 1, 2))
+                d[(a, b)] = dft.irfftn(mab * delta_k, s=shape, axes=(0, 1, 2))
         # Psi2_j = IDFT[-m_j DFT(src)]  ->  lam_src = IDFT[+sum_j m_j DFT(lam_psi2_j)]
-        ls = np.fft.irfftn(sum(mult[j] * np.fft.rfftn(lam_psi2[:, j].reshape(shape)) for j in range(3)),
+        ls = dft.irfftn(sum(mult[j] * dft.rfftn(lam_psi2[:, j].reshape(shape)) for j in range(3)),
                            s=shape, axes=(0, 1, 2))
         lam_d = {(0, 0): ls * (d[(1, 1)] + d[(2, 2)]), (1, 1): ls * (d[(0, 0)] + d[(2, 2)]),
                  (2, 2): ls * (d[(0, 0)] + d[(1, 1)]), (0, 1): -2 * ls * d[(0, 1)],
                  (0, 2): -2 * ls * d[(0, 2)], (1, 2): -2 * ls * d[(1, 2)]}
         for key, lv in lam_d.items():
-            acc = acc + mults[key] * amp * np.fft.rfftn(lv)   # even kernels: symmetric
-    return np.fft.irfftn(acc, s=shape, axes=(0, 1, 2))
+            acc = acc + mults[key] * amp * dft.rfftn(lv)   # even kernels: symmetric
+    return dft.irfftn(acc, s=shape, axes=(0, 1, 2))
 
 
 # ------------------------------------------------------------ full pipeline

@@ -26,6 +26,7 @@ import itertools
 import numpy as np
 
 from .cosmology import C_OVER_H0
+from . import dft
 from .lightcone import LensGeometry, apply_rotation, apply_transform, candidate_replicas, replica_transform
 from .lpt import _odd, linear_modes
 from .mesh import (cic_paint, cic_readout, cic_readout_grad, force_mesh, gradient_multipliers,
@@ -83,7 +84,7 @@ def lpt_tangent(delta_k, ddelta_k, nc, box, order):
     """(dPsi1, dPsi2) for a tangent ddelta_k of the linear modes."""
     shape = (nc, nc, nc)
     mult = gradient_multipliers(nc, box)
-    dpsi1 = np.stack([np.fft.irfftn(m * ddelta_k, s=shape, axes=(0, 1, 2)).ravel() for m in mult], axis=1)
+    dpsi1 = np.stack([dft.irfftn(m * ddelta_k, s=shape, axes=(0, 1, 2)).ravel() for m in mult], axis=1)
     if order == 1:
         return dpsi1, None
     kx, ky, kz = wavevectors(nc, box)
@@ -95,13 +96,13 @@ def lpt_tangent(delta_k, ddelta_k, nc, box, order):
     for i in range(3):
         for j in range(i, 3):
             mij = (-kk[i] * kk[i] if i == j else -_odd(kk[i], nc, box) * _odd(kk[j], nc, box)) * inv
-            d[(i, j)] = np.fft.irfftn(mij * delta_k, s=shape, axes=(0, 1, 2))
-            dd[(i, j)] = np.fft.irfftn(mij * ddelta_k, s=shape, axes=(0, 1, 2))
+            d[(i, j)] = dft.irfftn(mij * delta_k, s=shape, axes=(0, 1, 2))
+            dd[(i, j)] = dft.irfftn(mij * ddelta_k, s=shape, axes=(0, 1, 2))
     dsrc = (dd[(0, 0)] * d[(1, 1)] + d[(0, 0)] * dd[(1, 1)] + dd[(0, 0)] * d[(2, 2)] + d[(0, 0)] * dd[(2, 2)]
             + dd[(1, 1)] * d[(2, 2)] + d[(1, 1)] * dd[(2, 2)]
             - 2 * d[(0, 1)] * dd[(0, 1)] - 2 * d[(0, 2)] * dd[(0, 2)] - 2 * d[(1, 2)] * dd[(1, 2)])
-    sk = np.fft.rfftn(dsrc)
-    dpsi2 = np.stack([np.fft.irfftn(-m * sk, s=shape, axes=(0, 1, 2)).ravel() for m in mult], axis=1)
+    sk = dft.rfftn(dsrc)
+    dpsi2 = np.stack([dft.irfftn(-m * sk, s=shape, axes=(0, 1, 2)).ravel() for m in mult], axis=1)
     return dpsi1, dpsi2
 
 

@@ -25,6 +25,7 @@ from __future__ import annotations
 import numpy as np
 
 from .mesh import gradient_multipliers, wavevectors
+from . import dft
 
 
 def lattice(nc, box, nmesh):
@@ -40,7 +41,7 @@ def linear_modes(noise, cosmo, box):
     kx, ky, kz = wavevectors(nc, box)
     k = np.sqrt(kx ** 2 + ky ** 2 + kz ** 2)
     amp = np.sqrt(cosmo.pk_lin(k) * nc ** 3 / box ** 3)
-    dk = np.fft.rfftn(noise) * amp
+    dk = dft.rfftn(noise) * amp
     dk[0, 0, 0] = 0.0
     return dk
 
@@ -54,7 +55,7 @@ def lpt_displacements(delta_k, nc, box, order=1):
     """Psi1 (and Psi2 when order == 2) on the lattice, each (N, 3)."""
     shape = (nc, nc, nc)
     mult = gradient_multipliers(nc, box)
-    psi1 = np.stack([np.fft.irfftn(m * delta_k, s=shape, axes=(0, 1, 2)).ravel() for m in mult], axis=1)
+    psi1 = np.stack([dft.irfftn(m * delta_k, s=shape, axes=(0, 1, 2)).ravel() for m in mult], axis=1)
     if order == 1:
         return psi1, None
     kx, ky, kz = wavevectors(nc, box)
@@ -71,11 +72,11 @@ def lpt_displacements(delta_k, nc, box, order=1):
                 mult_ij = -kk[i] * kk[i] * inv
             else:
                 mult_ij = -_odd(kk[i], nc, box) * _odd(kk[j], nc, box) * inv
-            d[(i, j)] = np.fft.irfftn(mult_ij * delta_k, s=shape, axes=(0, 1, 2))
+            d[(i, j)] = dft.irfftn(mult_ij * delta_k, s=shape, axes=(0, 1, 2))
     src = (d[(0, 0)] * d[(1, 1)] + d[(0, 0)] * d[(2, 2)] + d[(1, 1)] * d[(2, 2)]
            - d[(0, 1)] ** 2 - d[(0, 2)] ** 2 - d[(1, 2)] ** 2)
-    sk = np.fft.rfftn(src)
-    psi2 = np.stack([np.fft.irfftn(-m * sk, s=shape, axes=(0, 1, 2)).ravel() for m in mult], axis=1)
+    sk = dft.rfftn(src)
+    psi2 = np.stack([dft.irfftn(-m * sk, s=shape, axes=(0, 1, 2)).ravel() for m in mult], axis=1)
     return psi1, psi2
 
 

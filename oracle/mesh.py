@@ -17,6 +17,7 @@ import itertools
 
 import numpy as np
 
+from . import dft
 
 def cic_paint(pos, nmesh, box, weight=1.0):
     """Cloud-in-cell paint of particles at pos (N, 3) [x, y, z] in Mpc/h."""
@@ -113,8 +114,8 @@ def force_mesh(delta_real, box, omega_m):
     the mean of delta is irrelevant (k = 0 is dropped).
     """
     nmesh = delta_real.shape[0]
-    dk = np.fft.rfftn(delta_real)
-    return [np.fft.irfftn(1.5 * omega_m * m * dk, s=delta_real.shape, axes=(0, 1, 2))
+    dk = dft.rfftn(delta_real)
+    return [dft.irfftn(1.5 * omega_m * m * dk, s=delta_real.shape, axes=(0, 1, 2))
             for m in gradient_multipliers(nmesh, box)]
 
 
@@ -138,9 +139,9 @@ def pgd_mesh(delta_real, box, alpha, k_l, k_s, n_s):
     parameter is the exponent n of the short-range filter.
     """
     nmesh = delta_real.shape[0]
-    dk = np.fft.rfftn(delta_real)
+    dk = dft.rfftn(delta_real)
     filt = pgd_filter(nmesh, box, k_l, k_s, n_s)
-    return [np.fft.irfftn(alpha * filt * m * dk, s=delta_real.shape, axes=(0, 1, 2))
+    return [dft.irfftn(alpha * filt * m * dk, s=delta_real.shape, axes=(0, 1, 2))
             for m in gradient_multipliers(nmesh, box)]
 
 

@@ -27,6 +27,7 @@ from __future__ import annotations
 
 import numpy as np
 
+from . import dft
 GAMMA = np.uint64(0x9E3779B97F4A7C15)
 
 
@@ -81,7 +82,7 @@ def angular_cl(maps, fov_deg: float, edges):
     n = maps.shape[-1]
     fov_rad = fov_deg * (np.pi / 180.0)
     omega_pix = (fov_rad / n) ** 2
-    power = omega_pix * np.abs(np.fft.fft2(maps)) ** 2 / n ** 2
+    power = omega_pix * np.abs(dft.fft2(maps)) ** 2 / n ** 2
     ell = multipole_of_modes(n, fov_deg)
     nb = len(edges) - 1
     cl = np.zeros(maps.shape[:-2] + (nb,))

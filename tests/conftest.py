@@ -9,6 +9,10 @@ if ROOT not in sys.path:
 
 
 def pytest_configure(config):
+    # the oracle's DFTs may use every host core (results do not depend on the count)
+    from oracle import dft
+    dft.set_workers(os.cpu_count() or 1)
+
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the built CUDA library")
     config.addinivalue_line("markers", "slow: long-running oracle case")
 
