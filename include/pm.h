@@ -281,8 +281,14 @@ const char* pm_kernel_name(int32_t kind);
  *  stream: cudaStream_t on which the work is enqueued; the call does not
  *          synchronise.
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  No cudaMalloc/cudaFree or allocating library routine is called.
+ * device, with that device current) and caches it.  With CUDA's lazy module
+ * loading the library's device code, and with it this array, is created on a
+ * device at the first call or kernel launch of the library there, so that
+ * first call may itself take device memory: make it before a hard memory
+ * budget is reached and before any stream capture.  The cached address does
+ * not survive cudaDeviceReset: do not call this entry point on a device that
+ * was reset after its first call.  No cudaMalloc/cudaFree or allocating
+ * library routine is called.
  * Every call shares the one array (its previous contents are overwritten;
  * the density is cleared on each call), so calls that overlap on the GPU --
  * on different streams or from different threads -- race and must be

@@ -1,5 +1,6 @@
 // Launchers of the 3D FFT passes and of the fused spectral operators.
 #include <algorithm>
+#include <mutex>
 
 #include "adjoint.h"
 #include "fft_impl.cuh"
@@ -8,6 +9,29 @@
 namespace pmlens {
 
 namespace {
+
+// Kernel attributes and occupancy belong to one device: they are set or
+// measured once per device (with that device current), thread-safely.
+constexpr int kMaxDevices = 64;
+
+int current_device() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) d = 0;
+  return d;
+}
+
+// resident block slots of a kernel on the current device (blocks per SM x SMs)
+template <typename K>
+int device_slots(std::once_flag* once, int* vals, K kernel, int threads, size_t smem) {
+  const int d = current_device();
+  std::call_once(once[d], [&] {
+    int per_sm = 0, nsm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, d);
+    vals[d] = std::max(per_sm, 1) * std::max(nsm, 1);
+  });
+  return vals[d];
+}
 
 template <typename R, int N>
 struct Launch {
@@ -24,34 +48,24 @@ struct Launch {
   using TT = TmaTile<R, N>;
   // persistent TMA column passes: one block per SM slot the occupancy allows
   static int tma_grid(int tiles) {
-    static const int slots = [] {
-      int per_sm = 0, dev = 0, nsm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_cols_tma<R, N, false, false>, TT::THREADS,
-                                                    TT::SMEM);
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      return std::max(per_sm, 1) * std::max(nsm, 1);
-    }();
-    return std::min(tiles, slots);
+    static std::once_flag once[kMaxDevices];
+    static int slots[kMaxDevices];
+    return std::min(tiles, device_slots(once, slots, k_fft_cols_tma<R, N, false, false>, TT::THREADS, TT::SMEM));
   }
 
   // persistent x c2r: every block slot the occupancy allows
   static int x_grid(int nblk) {
-    static const int slots = [] {
-      attrs();
-      int per_sm = 0, dev = 0, nsm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_x_c2r<R, N>, RowTile<R, N>::THREADS,
-                                                    smem_x());
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      return std::max(per_sm, 1) * std::max(nsm, 1);
-    }();
-    return std::min(nblk, slots);
+    attrs();
+    static std::once_flag once[kMaxDevices];
+    static int slots[kMaxDevices];
+    return std::min(nblk, device_slots(once, slots, k_fft_x_c2r<R, N>, RowTile<R, N>::THREADS, smem_x()));
   }
 
   static void attrs() {
-    static bool done = false;
-    if (done) return;
+    static std::once_flag once[kMaxDevices];
+    std::call_once(once[current_device()], set_attrs);
+  }
+  static void set_attrs() {
     cudaFuncSetAttribute(k_fft_x_r2c<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x());
     cudaFuncSetAttribute(k_fft_x_c2r<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_x());
     cudaFuncSetAttribute(k_fft_cols<R, N, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_cols());
@@ -65,7 +79,6 @@ struct Launch {
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          TT::SMEM_DUAL);
-    done = true;
   }
 
   static void x_fwd(const R* in, C* out, int P, cudaStream_t s, Prof* pf, int kind) {
@@ -99,14 +112,10 @@ struct Launch {
         !make_cols_map(&map2, d2, N, P, TT::W, TT::BOXR, false, sizeof(R) == 8))
       return cudaErrorInvalidValue;
     const int ntx = (N / 2 + 1 + TT::W - 1) / TT::W, tiles = ntx * N;
-    static const int slots = [] {
-      int per_sm = 0, dev = 0, nsm = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fft_cols_tma<R, N, true, false, true>, TT::THREADS,
-                                                    TT::SMEM_DUAL);
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      return std::max(per_sm, 1) * std::max(nsm, 1);
-    }();
+    static std::once_flag once[kMaxDevices];
+    static int slot_v[kMaxDevices];
+    const int slots =
+        device_slots(once, slot_v, k_fft_cols_tma<R, N, true, false, true>, TT::THREADS, (size_t)TT::SMEM_DUAL);
     k_fft_cols_tma<R, N, true, false, true><<<std::min(tiles, slots), TT::THREADS, TT::SMEM_DUAL, s>>>(
         map, map2, ntx, tiles, err, (R)kf);
     return cudaSuccess;
@@ -146,13 +155,9 @@ struct Launch {
         ok = make_cols_map(&om.m[q], o.p[q < npass ? oi[q] : 0], N, P, ZT::W, ZT::BOXR, true, sizeof(R) == 8);
       if (!ok) return cudaErrorInvalidValue;
       const int ntx = (N / 2 + 1 + ZT::W - 1) / ZT::W, tiles = ntx * N;
-      static const int slots = [] {
-        int per_sm = 0, dev = 0, nsm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_zpass_op_tma<R, N>, ZT::THREADS, ZT::SMEM);
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        return std::max(per_sm, 1) * std::max(nsm, 1);
-      }();
+      static std::once_flag once[kMaxDevices];
+      static int slot_v[kMaxDevices];
+      const int slots = device_slots(once, slot_v, k_zpass_op_tma<R, N>, ZT::THREADS, (size_t)ZT::SMEM);
       k_zpass_op_tma<R, N><<<std::min(tiles, slots), ZT::THREADS, ZT::SMEM, s>>>(in_map, om, ntx, tiles, npass, sp,
                                                                                  sp.err);
       return cudaSuccess;

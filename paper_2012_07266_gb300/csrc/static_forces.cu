@@ -26,7 +26,10 @@ std::mutex g_mu;
 void* g_scratch_addr[64] = {};
 
 // device address of the scratch array on the current device (looked up once
-// per device; the host-side symbol itself is not a device address)
+// per device; the host-side symbol itself is not a device address).  The
+// first lookup on a device loads the module there if no kernel of the library
+// has run on it yet (lazy loading); the cached address is stale after a
+// cudaDeviceReset, after which this entry point must not be used.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
