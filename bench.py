@@ -133,45 +133,80 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------- CPU baseline
-def cpu_baseline_sample(w, seed=0):
-    """The FP64 oracle as it stands on one kick-drift step + PM force of the
-    workload's particle count and mesh (the unit of the metric)."""
+PROJ_SUBSET = 16  # the shell projection is timed on every 16th particle and scaled by 16
+
+
+def cpu_baseline_sample(w, seed=0, workers=1):
+    """The FP64 oracle as it stands on one lightcone step of the workload (the
+    metric's unit of work, particle-steps, comes from whole steps): a kick-drift
+    step with the PM force of all particles on the workload's mesh, the PGD
+    displacement at the new positions, and the projection of one mid-lightcone
+    shell onto the workload's maps (timed on every PROJ_SUBSET-th particle and
+    scaled up: its cost is linear in the particles).  Returns the oracle's
+    particle-steps/s for a whole simulation (plain steps outside the lightcone,
+    lightcone steps inside it) and the seconds the sample took.  `workers`: the
+    threads the oracle's DFTs may use (its elementwise numpy work is
+    single-threaded either way)."""
+    from oracle import dft
     from oracle.cosmology import Cosmology
+    from oracle.lightcone import LensGeometry
     from oracle.lpt import lattice
-    from oracle.nbody import PMState, Stepper, kdk_step
+    from oracle.nbody import PMState, Stepper, kdk_step, pgd_displacement
+    dft.set_workers(workers)
     rng = np.random.default_rng(seed)
     nc, M, L = w["nc"], w["nmesh"], w["box"]
     cosmo = Cosmology(w["omega_m"], w["sigma8"], w["h"], w["n_s"], w["omega_b"], w["t_cmb"])
     st = Stepper(cosmo, w["a_init"], w["nsteps"])
+    geom = LensGeometry(cosmo, st, w["zs"], w["map_npix"], w["map_fov_deg"], L, nc, M,
+                        rotate=w.get("rotate", 1), seed=w.get("rotation_seed", 42),
+                        sub_evolution=w.get("sub_evolution", 1))
+    active = [i for i in range(w["nsteps"]) if geom.active(i)]
+    i = active[len(active) // 2]
     x = np.mod(lattice(nc, L, M) + rng.normal(0, 1.0, size=(nc ** 3, 3)), L)
     p = rng.normal(0, 1.0, size=(nc ** 3, 3))
     f = rng.normal(0, 1.0, size=(nc ** 3, 3))
     t0 = time.perf_counter()
-    kdk_step(PMState(x, p, f), 0, st, nc, M, L)
-    dt = time.perf_counter() - t0
-    return nc ** 3 / dt, dt
+    state = kdk_step(PMState(x, p, f), i, st, nc, M, L)
+    t1 = time.perf_counter()
+    S = pgd_displacement(state.x, st.a[i + 1], nc, M, L, w["pgd_params"]) if w.get("pgd") else None
+    t2 = time.perf_counter()
+    sub = slice(0, None, PROJ_SUBSET)
+    geom.project(i, state.x[sub], state.p[sub], None if S is None else S[sub])
+    t3 = time.perf_counter()
+    t_plain = t1 - t0
+    t_lens = (t2 - t1) + PROJ_SUBSET * (t3 - t2)
+    t_sim = w["nsteps"] * t_plain + len(active) * t_lens
+    return nc ** 3 * w["nsteps"] / t_sim, t3 - t0
+
+
+def cpu_sample_desc(w, workers, dt):
+    return (f"FP64 oracle, one lightcone step of {w['nc']}^3 particles on the {w['nmesh']}^3 mesh: kick-drift "
+            f"with the PM force, PGD, and one shell projected onto {len(w['zs'])} {w['map_npix']}^2 maps "
+            f"(timed on 1/{PROJ_SUBSET} of the particles and scaled); rate for a whole simulation of "
+            f"{w['nsteps']} steps from the plain and lightcone step times; DFTs on {workers} thread(s), "
+            f"elementwise numpy single-threaded; {dt:.1f} s")
 
 
 def run_reference(a, rank, world):
     if rank != 0:
         return
     w = bench_workload(a)
+    cores = os.cpu_count() or 1
     for _ in range(a.warmup):
-        cpu_baseline_sample(w)
-    times = []
+        cpu_baseline_sample(w, workers=cores)
+    rates, dts = [], []
     for k in range(a.steps):
-        _, dt = cpu_baseline_sample(w, seed=k)
-        times.append(dt)
-    t = sum(times) / len(times)
-    v = w["nc"] ** 3 / t
-    sample = (f"one kick-drift step with the PM force (paint, FFT Poisson+gradient, 3 inverse FFTs, "
-              f"readout) of {w['nc']}^3 particles on the {w['nmesh']}^3 mesh per step, FP64 numpy")
+        v, dt = cpu_baseline_sample(w, seed=k, workers=cores)
+        rates.append(v)
+        dts.append(dt)
+    v = float(np.mean(rates))
+    sample = cpu_sample_desc(w, cores, float(np.mean(dts)))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": w["nc"] ** 3 * w["nsteps"] / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{a.workload}: {WORKLOAD_DESC.get(a.workload, '')}",
                        "sample": "per step: " + sample},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -306,19 +341,29 @@ def run_gpu(a, rank, world, local_rank):
             "algo_bytes_per_launch": db / dn, "traffic": traffic}
     cpu = None
     if not a.no_cpu_baseline and world == 1:
-        v, dt = cpu_baseline_sample(w)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"one FP64 oracle kick-drift step with PM force of {w['nc']}^3 particles on the "
-                         f"{w['nmesh']}^3 mesh ({dt:.1f} s), single-threaded numpy"}
+        cores = os.cpu_count() or 1
+        v, dt = cpu_baseline_sample(w, workers=cores)
+        v1, dt1 = cpu_baseline_sample(w, workers=1)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": cpu_sample_desc(w, cores, dt),
+               "single_thread": {"value": v1, "cores": 1, "sample": cpu_sample_desc(w, 1, dt1)}}
     extra = {} if (a.no_extra or world > 1) else extra_legs(a, w, dev, rank)
-    # whole-step roofline against the byte model of a KDK step (paint, forward FFT,
-    # three inverse FFTs with the fused Poisson/gradient, readout + kick, drift):
-    # 9 R + 20 C + 100 N_p bytes, R = 4 M^3, C = 8 M^2 (M/2 + 1)
+    # whole-simulation roofline against the byte model of the path, R = 4 M^3, C = 8 M^2 (M/2 + 1):
+    # every KDK step (paint, forward FFT, three inverse FFTs with the fused Poisson/gradient,
+    # readout + kick, drift) 9 R + 20 C + 100 N_p; every lightcone step adds PGD (three inverse
+    # FFTs and the readout of three meshes) 3 (5 C + R) + 3 R + 12 N_p and the projection's read
+    # of the particle state 28 N_p
     M = w["nmesh"]
-    step_bytes = 9 * 4.0 * M ** 3 + 20 * 8.0 * M * M * (M // 2 + 1) + 100.0 * npart
-    at_peak = peak * 1e9 / step_bytes * npart
-    model = {"bytes_per_step_gb": round(step_bytes / 1e9, 2), "particle_steps_per_s_at_peak": at_peak,
-             "frac": round(value / (world * at_peak), 4), "peak_gbs": peak, "peak_source": peak_src}
+    R_, C_ = 4.0 * M ** 3, 8.0 * M * M * (M // 2 + 1)
+    kdk_bytes = 9 * R_ + 20 * C_ + 100.0 * npart
+    n_lens = prof.get("lens_project", (0, 0, 0))[1] // max(a.steps, 1)
+    lens_bytes = (3 * (5 * C_ + R_) + 3 * R_ + 12.0 * npart if w.get("pgd") else 0.0) + 28.0 * npart
+    sim_bytes = nsteps * kdk_bytes + n_lens * lens_bytes
+    at_peak = peak * 1e9 / sim_bytes * npart * nsteps
+    model = {"bytes_per_kdk_step_gb": round(kdk_bytes / 1e9, 2), "bytes_per_lightcone_step_extra_gb":
+             round(lens_bytes / 1e9, 2), "lightcone_steps": n_lens, "bytes_per_simulation_gb": round(sim_bytes / 1e9, 1),
+             "ms_per_simulation_at_peak": round(sim_bytes / (peak * 1e9) * 1e3, 2),
+             "particle_steps_per_s_at_peak": at_peak, "frac": round(value / (world * at_peak), 4),
+             "peak_gbs": peak, "peak_source": peak_src}
     maps_per_hour = world * 3600.0 / (ms * 1e-3) * len(w["zs"])  # one map per source plane
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -26,7 +26,9 @@ def test_reference_arm_json_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert abs(d["ms_per_step"] * 1e-3 * d["value"] - 64 ** 3) < 1e-6 * 64 ** 3   # one oracle step of 64^3
+    # ms_per_step: the oracle's time for one whole simulation (10 steps of 64^3 particles), the GPU arm's step
+    assert abs(d["ms_per_step"] * 1e-3 * d["value"] - 10 * 64 ** 3) < 1e-6 * 10 * 64 ** 3
+    assert "lightcone step" in cb["sample"]
 
 
 def test_reference_arm_other_ranks_are_silent():
