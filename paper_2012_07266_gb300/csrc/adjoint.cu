@@ -224,7 +224,7 @@ __global__ void k_lpt2_src_adj(const R* __restrict__ ls, const R* __restrict__ d
 // 256^3 adjoint).
 template <typename R>
 __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
-  const R cell_len = (R)A.cell_len, lo2 = (R)A.chi_lo2, hi2 = (R)A.chi_hi2;
+  const R cell_len = (R)A.cell_len;
   const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
   const R tan_half = (R)A.tan_half, margin = (R)A.margin;
   // whole warps iterate together (warp-level replica culling, as in the forward)
@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
     // one replica of this particle (the per-particle tests below decide exactly)
     auto project = [&](int q) {
       const Replica rp = A.rep[q];
-      R r[3];
+      R r[3], gf[3];
+      int gi[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const int ax = rp.perm[d];
@@ -257,10 +258,12 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
         }
         i += rp.shift[d];
         if (i >= A.M) i -= A.M;
-        r[d] = ((R)(i + rp.n[d] * A.M) + f) * cell_len;
+        gi[d] = i + rp.n[d] * A.M;
+        gf[d] = f;
+        r[d] = ((R)gi[d] + f) * cell_len;
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) return;
+      if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2))) return;
       const R lim = r[2] * tan_half + margin;
       if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
       if (A.S0 && !have_s) {

@@ -1352,6 +1352,13 @@ pm_status pm_profile_read(pm_ctx* c, double* ms, int64_t* launches, double* byte
   if (!c || nkinds < 0) return PM_ERR_ARG;
   if (cudaStreamSynchronize(c->stream)) return PM_ERR_CUDA;
   c->prof.resolve();
+  // the projection's PGD gathers: the mesh cells a gathering particle needs are its share
+  // M^3 / N_p of the three PGD meshes (neighbouring particles share corner cells)
+  unsigned long long ngath = 0;
+  if (cudaMemcpyAsync(&ngath, lens_gather_count(c), sizeof(ngath), cudaMemcpyDeviceToHost, c->stream) ||
+      cudaMemsetAsync(lens_gather_count(c), 0, sizeof(ngath), c->stream) || cudaStreamSynchronize(c->stream))
+    return PM_ERR_CUDA;
+  c->prof.bytes[KK_LENS] += (double)ngath * 3.0 * (double)c->rsz * (double)c->mesh_elems / (double)c->np;
   for (int k = 0; k < nkinds && k < KK_COUNT; ++k) {
     if (ms) ms[k] = c->prof.ms[k];
     if (launches) launches[k] = c->prof.launches[k];

@@ -187,7 +187,7 @@ struct LensTanArgs {
 // d(w cw_k) = dw/dchi_c dchi_c cw_k + w d cw_k, deposited on the same pixels.
 template <typename R>
 __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
-  const R cell_len = (R)A.cell_len, lo2 = (R)A.chi_lo2, hi2 = (R)A.chi_hi2;
+  const R cell_len = (R)A.cell_len;
   const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
   const R tan_half = (R)A.tan_half, margin = (R)A.margin;
   const R* fr = reinterpret_cast<const R*>(A.st.frac);
@@ -208,8 +208,9 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
     const WarpBox box = warp_box(valid, (float)ci0 + (float)cf0, (float)ci1 + (float)cf1, (float)ci2 + (float)cf2);
     auto project = [&](int q) {
       const Replica rp = A.rep[q];
-      R r[3], pr[3], dr[3], dpr[3];
+      R r[3], pr[3], dr[3], dpr[3], gf[3];
       R sg[3];
+      int gi[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const int ax = rp.perm[d];
@@ -223,13 +224,15 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
         }
         i += rp.shift[d];
         if (i >= A.M) i -= A.M;
-        r[d] = ((R)(i + rp.n[d] * A.M) + f) * cell_len;
+        gi[d] = i + rp.n[d] * A.M;
+        gf[d] = f;
+        r[d] = ((R)gi[d] + f) * cell_len;
         pr[d] = sg[d] * pick3(ax, cp0, cp1, cp2);
         dr[d] = sg[d] * pick3(ax, tx0, tx1, tx2) * cell_len;
         dpr[d] = sg[d] * pick3(ax, tp0, tp1, tp2);
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) return;
+      if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2))) return;
       const R lim = r[2] * tan_half + margin;
       if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
       if (A.S0 && !have_s) {

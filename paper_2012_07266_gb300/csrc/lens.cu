@@ -49,6 +49,7 @@ struct LensArgs {
   unsigned nz_mask;   // bit s: source s is a distribution n(z) (weight from var.qtab)
   double* maps;
   int* flag;
+  unsigned long long* gathers;  // count of PGD gathers (forward projection), or null
   const double* lam;  // when set: accumulate sum(lam * increment) into var[v].acc instead of the maps
   int nrep;
   Replica rep[kMaxReplicas];
@@ -103,12 +104,13 @@ __device__ __forceinline__ R gather3(const R* __restrict__ m, int M, int ix, int
 // shell selection and the PGD gather (NV = 2: the Omega_m +/- h dot products).
 template <typename R, int NV>
 __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
-  const R cell_len = (R)A.cell_len, lo2 = (R)A.chi_lo2, hi2 = (R)A.chi_hi2;
+  const R cell_len = (R)A.cell_len;
   const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
   const R tan_half = (R)A.tan_half, margin = (R)A.margin;
   R dot[NV];
 #pragma unroll
   for (int vi = 0; vi < NV; ++vi) dot[vi] = R(0);
+  unsigned ngath = 0;  // particles of this thread whose PGD displacement was gathered
   // whole warps iterate together (warp-level replica culling); lanes past the end add nothing
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -127,7 +129,8 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
     // one replica of this particle (the per-particle tests below decide exactly)
     auto project = [&](int q) {
       const Replica rp = A.rep[q];
-      R r[3], pr[3], sr[3];
+      R r[3], pr[3], sr[3], gf[3];
+      int gi[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const int ax = rp.perm[d];
@@ -141,12 +144,14 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         }
         i += rp.shift[d];
         if (i >= A.M) i -= A.M;
-        r[d] = ((R)(i + rp.n[d] * A.M) + f) * cell_len;
+        gi[d] = i + rp.n[d] * A.M;
+        gf[d] = f;
+        r[d] = ((R)gi[d] + f) * cell_len;
         pr[d] = sg * pick3(ax, cp0, cp1, cp2);
         sr[d] = sg * pick3(ax, cs0, cs1, cs2);
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      if (!(chi2 > lo2 && chi2 <= hi2 && r[2] > R(0))) return;
+      if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2))) return;
       // outside the field of view by more than the displacement margin: no weight on the map
       const R lim = r[2] * tan_half + margin;
       if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
@@ -155,6 +160,7 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         cs1 = gather3(A.S1, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
         cs2 = gather3(A.S2, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
         have_s = true;
+        ++ngath;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const R v = pick3((int)rp.perm[d], cs0, cs1, cs2);
@@ -229,6 +235,10 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
       }
     }
   }
+  if (A.gathers) {  // the particle loop is warp-uniform: every lane arrives here
+    const unsigned t = __reduce_add_sync(0xffffffffu, ngath);
+    if (lane == 0 && t) atomicAdd(A.gathers, (unsigned long long)t);
+  }
   if (A.lam) {
 #pragma unroll
     for (int vi = 0; vi < NV; ++vi) {
@@ -259,9 +269,10 @@ cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
   fill_lens_args<R>(c, sh, use_pgd, A);
   long long blocks = (c->np + 255) / 256;
   if (blocks > 152LL * 8) blocks = 152LL * 8;
-  // particle state read once (+ three PGD meshes gathered)
-  ProfScope ps(&c->prof, KK_LENS, c->stream,
-               c->np * (4.0 + 6.0 * sizeof(R)) + (use_pgd ? 3.0 * c->mesh_elems * sizeof(R) : 0.0));
+  // particle state read once; the PGD gathers (mesh bytes in proportion to the particles
+  // that gathered, counted on the device) are booked when the profile is read
+  A.gathers = use_pgd ? lens_gather_count(c) : nullptr;
+  ProfScope ps(&c->prof, KK_LENS, c->stream, c->np * (4.0 + 6.0 * sizeof(R)));
   k_lens<R, 1><<<(int)blocks, 256, 0, c->stream>>>(A);
   return cudaGetLastError();
 }
@@ -334,6 +345,7 @@ static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs
   A.tab_n = kChiTab;
   A.maps = reinterpret_cast<double*>(c->ws + c->L.maps);
   A.flag = flags_ptr(c);
+  A.gathers = nullptr;
   A.nz_mask = c->nz_mask;
   A.lam = nullptr;
   A.nrep = sh.nrep;

@@ -42,6 +42,32 @@ __device__ __forceinline__ WarpBox warp_box(bool valid, float p0, float p1, floa
   return b;
 }
 
+// Shell membership, chi^2 in (lo2, hi2], of the replica position (gi + f) cells
+// (gi: integer cell including the replica offset, f: fraction).  In FP32 a
+// position thousands of cells from the observer carries a rounding of ~1e-7 of
+// its distance, which near a shell boundary decides membership differently from
+// exact arithmetic (and the affected particle's whole weight moves between
+// shells); within 1e-6 (relative, in chi^2) of either boundary the test is
+// redone in FP64, so that both precisions select the same particles.  The
+// forward, reverse and tangent projections share this test.
+template <typename R>
+__device__ __forceinline__ bool in_shell(R chi2, const int (&gi)[3], const R (&f)[3], double cell_len, double lo2,
+                                         double hi2) {
+  if constexpr (sizeof(R) == 8) {
+    return chi2 > lo2 && chi2 <= hi2;
+  } else {
+    const float band = 1e-6f * chi2;
+    if (fabsf(chi2 - (float)lo2) > band && fabsf(chi2 - (float)hi2) > band) return chi2 > (float)lo2 && chi2 <= (float)hi2;
+    double c2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double x = ((double)gi[d] + (double)f[d]) * cell_len;
+      c2 += x * x;
+    }
+    return c2 > lo2 && c2 <= hi2;
+  }
+}
+
 // false only if no position in the box can pass the shell, z > 0 and field-of-view
 // tests of the per-particle code under replica rp
 __device__ __forceinline__ bool replica_may_hit(const Replica& rp, const WarpBox& b, int M, float cell_len,

@@ -262,6 +262,11 @@ inline const R* chi_table(pm_ctx* c, int id) {
 }
 inline int* flags_ptr(pm_ctx* c) { return reinterpret_cast<int*>(c->ws + c->L.flags); }
 inline int* timeout_ptr(pm_ctx* c) { return flags_ptr(c) + 1; }
+// particles whose PGD displacement the projection gathered since the last profile read
+// (they bound the mesh bytes its gathers must move)
+inline unsigned long long* lens_gather_count(pm_ctx* c) {
+  return reinterpret_cast<unsigned long long*>(c->ws + c->L.flags + 64);
+}
 // q tables of the n(z) sources, kind 0: q(chi), 1: dq/dchi, 2: q at Omega_m + h, 3: at
 // Omega_m - h; n_zs * kChiTab entries per kind (source s at s * kChiTab)
 enum QKind { Q_CENTRAL = 0, Q_DERIV = 1, Q_PLUS = 2, Q_MINUS = 3 };

@@ -4,9 +4,12 @@
 // particles no longer sit in neighbouring cells and the CIC gathers/scatters of
 // a step re-fetch mesh lines from HBM several times.  Every few steps the state
 // is counting-sorted by coarse block of 8^3 force-mesh cells (row-major block
-// order): count, exclusive scan, scatter into the second state buffer.  The
-// original index of each particle travels along (pid), so outputs and the
-// initial-condition adjoint stay in lattice order.
+// order): count, exclusive scan, scatter into the second state buffer.  (A
+// Morton block order, which keeps a thread block's run of particles in a
+// compact region, measured 10% less DRAM traffic in kick-drift-paint but a 12%
+// slower launch at pm256, so row-major order stays.)  The original index of
+// each particle travels along (pid), so outputs and the initial-condition
+// adjoint stay in lattice order.
 #include <algorithm>
 
 #include "pm_internal.h"
@@ -21,6 +24,8 @@ __device__ __forceinline__ unsigned bucket_of(uint32_t c, int nbs) {
   const unsigned ix = c & 1023u, iy = (c >> 10) & 1023u, iz = c >> 20;
   return ((iz / kBlk) * nbs + iy / kBlk) * nbs + ix / kBlk;
 }
+
+inline long long buckets_per_side(int M) { return (M + kBlk - 1) / kBlk; }
 
 __global__ void __launch_bounds__(256) k_bucket_count(const uint32_t* __restrict__ cell, long long np, int nbs,
                                                       unsigned* __restrict__ count) {
@@ -155,7 +160,7 @@ void launch_iota(pm_ctx* c) {
 
 template <typename R>
 cudaError_t sort_particles(pm_ctx* c) {
-  const int nbs = (c->M + kBlk - 1) / kBlk;
+  const int nbs = (int)buckets_per_side(c->M);
   const long long nb = (long long)nbs * nbs * nbs;
   unsigned* count = reinterpret_cast<unsigned*>(c->ws + c->L.sort_cnt);
   unsigned* offs = count + nb;
@@ -203,7 +208,7 @@ cudaError_t launch_permute3(pm_ctx* c, const R* src, const uint32_t* pid, R* dst
 }
 
 size_t sort_scratch_bytes(int M) {
-  const long long nbs = (M + kBlk - 1) / kBlk;
+  const long long nbs = buckets_per_side(M);
   const long long nb = nbs * nbs * nbs;
   return (size_t)(2 * nb + (nb + 1023) / 1024 + 1024) * sizeof(unsigned);
 }
