@@ -54,6 +54,8 @@ def args_():
     ap.add_argument("--pgd", type=int, default=None, help="override PGD on/off (profiling cases)")
     ap.add_argument("--no-extra", action="store_true", help="skip the adjoint, FP64 and serving legs")
     ap.add_argument("--serve-requests", type=int, default=40)
+    ap.add_argument("--cpu-single-thread", action="store_true",
+                    help="also time the oracle baseline with one DFT thread")
     return ap.parse_args()
 
 
@@ -133,79 +135,161 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------- CPU baseline
-PROJ_SUBSET = 16  # the shell projection is timed on every 16th particle and scaled by 16
+PROJ_SUBSET = 16          # the shell projection is timed on every 16th particle and scaled by 16
+STEP_SUBSETS = (8, 16)    # kick-drift and PGD timed on every 8th and 16th particle, then fitted
+
+
+class OracleSample:
+    """The FP64 oracle as it stands on the work of one lightcone step of the
+    workload (the metric's unit of work, particle-steps, comes from whole steps):
+    a kick-drift step with the PM force on the workload's mesh, the PGD
+    displacement at the new positions, and the projection of one mid-lightcone
+    shell onto the workload's maps.  Kick-drift and PGD are timed with 1/8 and
+    1/16 of the particles on the full mesh and extrapolated to all particles by
+    the affine fit t = a + b N (the mesh work is the same, CIC paint and readout
+    are linear in N; when noise makes the fit unphysical, the larger subset is
+    scaled in proportion, an upper bound on the time); the projection is timed
+    on 1/PROJ_SUBSET of the particles and scaled (linear in N).  `workers`: the
+    threads the oracle's DFTs may use (its elementwise numpy work is
+    single-threaded either way)."""
+
+    def __init__(self, w, seed=0, workers=1):
+        from oracle import dft
+        from oracle.cosmology import Cosmology
+        from oracle.lightcone import LensGeometry
+        from oracle.lpt import lattice
+        from oracle.nbody import PMState, Stepper, kdk_step, pgd_displacement
+        self._kdk, self._pgd, self._state = kdk_step, pgd_displacement, PMState
+        dft.set_workers(workers)
+        self.w, self.workers = w, workers
+        rng = np.random.default_rng(seed)
+        self.nc, self.M, self.L = w["nc"], w["nmesh"], w["box"]
+        self.npart = self.nc ** 3
+        cosmo = Cosmology(w["omega_m"], w["sigma8"], w["h"], w["n_s"], w["omega_b"], w["t_cmb"])
+        self.st = Stepper(cosmo, w["a_init"], w["nsteps"])
+        self.geom = LensGeometry(cosmo, self.st, w["zs"], w["map_npix"], w["map_fov_deg"], self.L, self.nc, self.M,
+                                 rotate=w.get("rotate", 1), seed=w.get("rotation_seed", 42),
+                                 sub_evolution=w.get("sub_evolution", 1))
+        self.active = [i for i in range(w["nsteps"]) if self.geom.active(i)]
+        self.i = self.active[len(self.active) // 2]
+        self.x = np.mod(lattice(self.nc, self.L, self.M) + rng.normal(0, 1.0, size=(self.npart, 3)), self.L)
+        self.p = rng.normal(0, 1.0, size=(self.npart, 3))
+        self.f = rng.normal(0, 1.0, size=(self.npart, 3))
+        self.S = rng.normal(0, 0.1, size=(self.npart, 3))
+        self.t = {}      # component -> extrapolated seconds
+        self.fits = {}
+
+    def _extrapolate(self, name, ts, ns):
+        b = (ts[0] - ts[1]) / (ns[0] - ns[1])
+        a = ts[0] - b * ns[0]
+        if b > 0 and a > 0:
+            self.fits[name] = "affine"
+            return a + b * self.npart
+        self.fits[name] = "proportional"
+        return ts[0] * self.npart / ns[0]
+
+    def kick_drift(self):
+        i, ts, ns = self.i, [], []
+        for sub in STEP_SUBSETS:
+            sl = slice(0, None, sub)
+            t0 = time.perf_counter()
+            self._kdk(self._state(self.x[sl], self.p[sl], self.f[sl]), i, self.st, self.nc, self.M, self.L)
+            ts.append(time.perf_counter() - t0)
+            ns.append(len(self.x[sl]))
+        self.t["kick_drift"] = self._extrapolate("kick_drift", ts, ns)
+
+    def pgd(self):
+        if not self.w.get("pgd"):
+            self.t["pgd"] = 0.0
+            return
+        i, ts, ns = self.i, [], []
+        for sub in STEP_SUBSETS:
+            sl = slice(0, None, sub)
+            t0 = time.perf_counter()
+            self._pgd(self.x[sl], self.st.a[i + 1], self.nc, self.M, self.L, self.w["pgd_params"])
+            ts.append(time.perf_counter() - t0)
+            ns.append(len(self.x[sl]))
+        self.t["pgd"] = self._extrapolate("pgd", ts, ns)
+
+    def projection(self):
+        sl = slice(0, None, PROJ_SUBSET)
+        t0 = time.perf_counter()
+        self.geom.project(self.i, self.x[sl], self.p[sl], self.S[sl] if self.w.get("pgd") else None)
+        self.t["projection"] = PROJ_SUBSET * (time.perf_counter() - t0)
+
+    def warm(self):
+        """Untimed pass on 1/32 of the particles: the mesh-sized arrays' memory is touched once."""
+        sl = slice(0, None, 32)
+        self._kdk(self._state(self.x[sl], self.p[sl], self.f[sl]), self.i, self.st, self.nc, self.M, self.L)
+        if self.w.get("pgd"):
+            self._pgd(self.x[sl], self.st.a[self.i + 1], self.nc, self.M, self.L, self.w["pgd_params"])
+
+    COMPONENTS = ("kick_drift", "pgd", "projection")
+
+    def run(self, component):
+        getattr(self, component)()
+
+    def rate(self):
+        """Particle-steps/s of a whole simulation: plain steps outside the lightcone, lightcone steps inside."""
+        w = self.w
+        t_sim = w["nsteps"] * self.t["kick_drift"] + len(self.active) * (self.t["pgd"] + self.t["projection"])
+        return self.npart * w["nsteps"] / t_sim, t_sim
+
+    def describe(self, dt):
+        w, t = self.w, self.t
+        return (f"FP64 oracle, the work of one lightcone step of {w['nc']}^3 particles on the {w['nmesh']}^3 mesh: "
+                f"kick-drift with the PM force ({t.get('kick_drift', 0):.1f} s), PGD ({t.get('pgd', 0):.1f} s) and "
+                f"one shell projected onto {len(w['zs'])} {w['map_npix']}^2 maps ({t.get('projection', 0):.1f} s), "
+                f"extrapolated to all particles from timings with 1/8 and 1/16 of them (kick-drift, PGD: "
+                f"{self.fits.get('kick_drift', '-')}/{self.fits.get('pgd', '-')}) or 1/{PROJ_SUBSET} (projection, "
+                f"linear); rate for a whole simulation of {w['nsteps']} steps ({len(self.active)} in the lightcone); "
+                f"DFTs on {self.workers} thread(s), elementwise numpy single-threaded; {dt:.1f} s of timing")
 
 
 def cpu_baseline_sample(w, seed=0, workers=1):
-    """The FP64 oracle as it stands on one lightcone step of the workload (the
-    metric's unit of work, particle-steps, comes from whole steps): a kick-drift
-    step with the PM force of all particles on the workload's mesh, the PGD
-    displacement at the new positions, and the projection of one mid-lightcone
-    shell onto the workload's maps (timed on every PROJ_SUBSET-th particle and
-    scaled up: its cost is linear in the particles).  Returns the oracle's
-    particle-steps/s for a whole simulation (plain steps outside the lightcone,
-    lightcone steps inside it) and the seconds the sample took.  `workers`: the
-    threads the oracle's DFTs may use (its elementwise numpy work is
-    single-threaded either way)."""
-    from oracle import dft
-    from oracle.cosmology import Cosmology
-    from oracle.lightcone import LensGeometry
-    from oracle.lpt import lattice
-    from oracle.nbody import PMState, Stepper, kdk_step, pgd_displacement
-    dft.set_workers(workers)
-    rng = np.random.default_rng(seed)
-    nc, M, L = w["nc"], w["nmesh"], w["box"]
-    cosmo = Cosmology(w["omega_m"], w["sigma8"], w["h"], w["n_s"], w["omega_b"], w["t_cmb"])
-    st = Stepper(cosmo, w["a_init"], w["nsteps"])
-    geom = LensGeometry(cosmo, st, w["zs"], w["map_npix"], w["map_fov_deg"], L, nc, M,
-                        rotate=w.get("rotate", 1), seed=w.get("rotation_seed", 42),
-                        sub_evolution=w.get("sub_evolution", 1))
-    active = [i for i in range(w["nsteps"]) if geom.active(i)]
-    i = active[len(active) // 2]
-    x = np.mod(lattice(nc, L, M) + rng.normal(0, 1.0, size=(nc ** 3, 3)), L)
-    p = rng.normal(0, 1.0, size=(nc ** 3, 3))
-    f = rng.normal(0, 1.0, size=(nc ** 3, 3))
+    """One whole oracle sample (all three components); returns (particle-steps/s, seconds, sample)."""
+    smp = OracleSample(w, seed, workers)
+    smp.warm()
     t0 = time.perf_counter()
-    state = kdk_step(PMState(x, p, f), i, st, nc, M, L)
-    t1 = time.perf_counter()
-    S = pgd_displacement(state.x, st.a[i + 1], nc, M, L, w["pgd_params"]) if w.get("pgd") else None
-    t2 = time.perf_counter()
-    sub = slice(0, None, PROJ_SUBSET)
-    geom.project(i, state.x[sub], state.p[sub], None if S is None else S[sub])
-    t3 = time.perf_counter()
-    t_plain = t1 - t0
-    t_lens = (t2 - t1) + PROJ_SUBSET * (t3 - t2)
-    t_sim = w["nsteps"] * t_plain + len(active) * t_lens
-    return nc ** 3 * w["nsteps"] / t_sim, t3 - t0
-
-
-def cpu_sample_desc(w, workers, dt):
-    return (f"FP64 oracle, one lightcone step of {w['nc']}^3 particles on the {w['nmesh']}^3 mesh: kick-drift "
-            f"with the PM force, PGD, and one shell projected onto {len(w['zs'])} {w['map_npix']}^2 maps "
-            f"(timed on 1/{PROJ_SUBSET} of the particles and scaled); rate for a whole simulation of "
-            f"{w['nsteps']} steps from the plain and lightcone step times; DFTs on {workers} thread(s), "
-            f"elementwise numpy single-threaded; {dt:.1f} s")
+    for comp in OracleSample.COMPONENTS:
+        smp.run(comp)
+    dt = time.perf_counter() - t0
+    return smp.rate()[0], dt, smp
 
 
 def run_reference(a, rank, world):
+    """The oracle on the host cores.  Each step times one component of the lightcone step's
+    work in rotation (kick-drift, PGD, projection), so that a step stays at ~20 s; the rate
+    combines the mean time of each component (components no timed step reached are timed
+    once after the steps)."""
     if rank != 0:
         return
     w = bench_workload(a)
     cores = os.cpu_count() or 1
-    for _ in range(a.warmup):
-        cpu_baseline_sample(w, workers=cores)
-    rates, dts = [], []
+    smp = OracleSample(w, workers=cores)
+    smp.warm()
+    comps = OracleSample.COMPONENTS
+    for k in range(a.warmup):
+        smp.run(comps[k % 3])
+    acc = {c: [] for c in comps}
+    t0 = time.perf_counter()
     for k in range(a.steps):
-        v, dt = cpu_baseline_sample(w, seed=k, workers=cores)
-        rates.append(v)
-        dts.append(dt)
-    v = float(np.mean(rates))
-    sample = cpu_sample_desc(w, cores, float(np.mean(dts)))
+        smp.run(comps[k % 3])
+        acc[comps[k % 3]].append(smp.t[comps[k % 3]])
+    for c in comps:
+        if not acc[c]:
+            smp.run(c)
+            acc[c].append(smp.t[c])
+    dt = time.perf_counter() - t0
+    for c in comps:
+        smp.t[c] = float(np.mean(acc[c]))
+    v, t_sim = smp.rate()
+    sample = smp.describe(dt)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
-            "steps": a.steps, "warmup": a.warmup, "ms_per_step": w["nc"] ** 3 * w["nsteps"] / v * 1e3,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_sim * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"{a.workload}: {WORKLOAD_DESC.get(a.workload, '')}",
-                       "sample": "per step: " + sample},
+                       "sample": "each step one component of the lightcone step in rotation; " + sample},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -342,10 +426,11 @@ def run_gpu(a, rank, world, local_rank):
     cpu = None
     if not a.no_cpu_baseline and world == 1:
         cores = os.cpu_count() or 1
-        v, dt = cpu_baseline_sample(w, workers=cores)
-        v1, dt1 = cpu_baseline_sample(w, workers=1)
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": cpu_sample_desc(w, cores, dt),
-               "single_thread": {"value": v1, "cores": 1, "sample": cpu_sample_desc(w, 1, dt1)}}
+        v, dt, smp = cpu_baseline_sample(w, workers=cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp.describe(dt)}
+        if a.cpu_single_thread:
+            v1, dt1, smp1 = cpu_baseline_sample(w, workers=1)
+            cpu["single_thread"] = {"value": v1, "cores": 1, "sample": smp1.describe(dt1)}
     extra = {} if (a.no_extra or world > 1) else extra_legs(a, w, dev, rank)
     # whole-simulation roofline against the byte model of the path, R = 4 M^3, C = 8 M^2 (M/2 + 1):
     # every KDK step (paint, forward FFT, three inverse FFTs with the fused Poisson/gradient,
@@ -413,11 +498,19 @@ def extra_legs(a, w, dev, rank):
             t_f += e0.elapsed_time(e1)
             t_fa += e0.elapsed_time(e2)
         t_f, t_fa = t_f / reps, t_fa / reps
+        # kernel classes of one reverse sweep (library CUDA-event profile)
+        sim.run(noise)
+        sim.profile_read()
+        sim.profile(True)
+        sim.vjp(lam)
+        sim.profile(False)
+        classes = {kk: {"ms": round(v[0], 2), "launches": v[1]} for kk, v in sim.profile_read().items() if v[1]}
         gb = sim.nbytes / 1e9
         del sim
         torch.cuda.empty_cache()
         return {"value": npart * nsteps / (t_fa * 1e-3), "unit": UNIT, "ms_per_step": t_fa, "forward_ms": t_f,
-                "adjoint_over_forward": (t_fa - t_f) / t_f, "checkpoint_every": ckpt, "workspace_gb": gb}, k
+                "adjoint_over_forward": (t_fa - t_f) / t_f, "checkpoint_every": ckpt, "workspace_gb": gb,
+                "adjoint_kernel_classes": classes}, k
 
     out["fwd_adjoint"], k = time_fwd_adj(nsteps)
     out["fwd_adjoint_ckpt4"], _ = time_fwd_adj(4)

@@ -410,14 +410,14 @@ static int blocks_for(long long n) {
 template <typename R>
 void adj_paint_weights(const AdjState<R>& s, const R* v, R* const* meshes, int M, long long np, cudaStream_t st,
                        Prof* pf) {
-  ProfScope ps(pf, KK_ADJ, st, np * (4.0 + 6.0 * sizeof(R)) + 3.0 * (double)M * M * M * sizeof(R));
+  ProfScope ps(pf, KK_ADJ_PAINT, st, np * (4.0 + 6.0 * sizeof(R)) + 3.0 * (double)M * M * M * sizeof(R));
   k_paint_weights<R><<<blocks_for(np), 256, 0, st>>>(s, v, v + np, v + 2 * np, meshes[0], meshes[1], meshes[2], M, np);
 }
 
 template <typename R>
 void adj_readout_grad(const AdjState<R>& s, R* const* meshes, const R* v, const R* phi, double mass, R* lx,
                       const R* lp, double* dot, int M, long long np, cudaStream_t st, Prof* pf) {
-  ProfScope ps(pf, KK_ADJ, st, np * (4.0 + 12.0 * sizeof(R)) + 4.0 * (double)M * M * M * sizeof(R));
+  ProfScope ps(pf, KK_ADJ_READ, st, np * (4.0 + 12.0 * sizeof(R)) + 4.0 * (double)M * M * M * sizeof(R));
   k_readout_grad<R><<<blocks_for(np), 256, 0, st>>>(s, meshes[0], meshes[1], meshes[2], v, v + np, v + 2 * np, phi,
                                                    (R)mass, lx, lp, dot, M, np);
 }

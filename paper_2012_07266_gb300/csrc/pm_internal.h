@@ -59,7 +59,8 @@ struct LensShell {
 // kernel classes for launch counting and optional event timing
 enum KernelKind {
   KK_KDK_PAINT = 0, KK_PAINT, KK_FFT_X_FWD, KK_FFT_Y_FWD, KK_FFT_Z_FWD, KK_FFT_Z_OP, KK_FFT_Y_INV,
-  KK_FFT_X_INV, KK_LENS, KK_IC, KK_MISC, KK_ADJ, KK_ADJ_FFT, KK_ADJ_LENS, KK_JVP, KK_COUNT
+  KK_FFT_X_INV, KK_LENS, KK_IC, KK_MISC, KK_ADJ, KK_ADJ_FFT, KK_ADJ_LENS, KK_JVP, KK_ADJ_PAINT, KK_ADJ_READ,
+  KK_COUNT
 };
 const char* kernel_kind_name(int k);
 

@@ -7,7 +7,7 @@ const char* kernel_kind_name(int k) {
   static const char* names[KK_COUNT] = {"kick_drift_paint", "paint", "fft_x_r2c", "fft_y_fwd", "fft_z_fwd",
                                         "fft_z_spectral_op", "fft_y_inv", "fft_x_c2r", "lens_project", "ic",
                                         "misc", "adjoint_particles", "adjoint_spectral", "adjoint_lens",
-                                        "tangent"};
+                                        "tangent", "adjoint_paint", "adjoint_readout"};
   return (k >= 0 && k < KK_COUNT) ? names[k] : "unknown";
 }
 
