@@ -431,7 +431,7 @@ def run_gpu(a, rank, world, local_rank):
         if a.cpu_single_thread:
             v1, dt1, smp1 = cpu_baseline_sample(w, workers=1)
             cpu["single_thread"] = {"value": v1, "cores": 1, "sample": smp1.describe(dt1)}
-    extra = {} if (a.no_extra or world > 1) else extra_legs(a, w, dev, rank)
+    extra = {} if (a.no_extra or world > 1) else extra_legs(a, w, dev, rank, ms)
     # whole-simulation roofline against the byte model of the path, R = 4 M^3, C = 8 M^2 (M/2 + 1):
     # every KDK step (paint, forward FFT, three inverse FFTs with the fused Poisson/gradient,
     # readout + kick, drift) 9 R + 20 C + 100 N_p; every lightcone step adds PGD (three inverse
@@ -465,7 +465,7 @@ def run_gpu(a, rank, world, local_rank):
         dist.destroy_process_group()
 
 
-def extra_legs(a, w, dev, rank):
+def extra_legs(a, w, dev, rank, forward_ms):
     """Forward + adjoint at the same workload, forward mode, the plain FP64
     path, the shot-noise estimate, and the serving mix (Poisson arrivals, mixed
     sizes and cosmologies)."""
@@ -508,9 +508,12 @@ def extra_legs(a, w, dev, rank):
         gb = sim.nbytes / 1e9
         del sim
         torch.cuda.empty_cache()
+        # the reverse sweep's time, against this leg's forward and against the main timed forward
+        # (the leg times two runs only, so its forward carries more run-to-run spread)
         return {"value": npart * nsteps / (t_fa * 1e-3), "unit": UNIT, "ms_per_step": t_fa, "forward_ms": t_f,
-                "adjoint_over_forward": (t_fa - t_f) / t_f, "checkpoint_every": ckpt, "workspace_gb": gb,
-                "adjoint_kernel_classes": classes}, k
+                "adjoint_ms": t_fa - t_f, "adjoint_over_forward": (t_fa - t_f) / t_f,
+                "adjoint_over_main_forward": (t_fa - t_f) / forward_ms, "checkpoint_every": ckpt,
+                "workspace_gb": gb, "adjoint_kernel_classes": classes}, k
 
     out["fwd_adjoint"], k = time_fwd_adj(nsteps)
     out["fwd_adjoint_ckpt4"], _ = time_fwd_adj(4)

@@ -100,15 +100,65 @@ __global__ void k_paint_weights(AdjState<R> s, const R* __restrict__ v0, const R
   if (j < np) one(j);
 }
 
+// the three cotangent components into one interleaved float4 mesh: per corner one
+// 16-byte reduction carries x, y, z (12 vector reductions per particle become 8; the
+// reductions' L2 throughput bounds this kernel)
+__global__ void __launch_bounds__(256) k_paint_weights4(AdjState<float> s, const float* __restrict__ v0,
+                                                        const float* __restrict__ v1, const float* __restrict__ v2,
+                                                        float* __restrict__ m4, int M, long long np) {
+  auto one = [&](long long j) {
+    int i[3];
+    unpack3(s.cell[j], i);
+    const Corners c = corners(M, i[0], i[1], i[2]);
+    const float fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
+    const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
+    const float a = v0[j], b = v1[j], d = v2[j];
+    const unsigned rows[4] = {c.r00, c.r01, c.r10, c.r11};
+    const float wr[4] = {gz * gy, gz * fy, fz * gy, fz * fy};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const float w = wr[q] * (dx ? fx : gx);
+        float* p = m4 + 4ull * (rows[q] + (dx ? c.x1 : c.x0));
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(w * a), "f"(w * b), "f"(w * d),
+                     "f"(0.f)
+                     : "memory");
+      }
+    }
+  };
+  // two independent particles per iteration (overlapping their loads and reductions)
+  const long long S = (long long)gridDim.x * blockDim.x;
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; j + S < np; j += 2 * S) {
+    one(j);
+    one(j + S);
+  }
+  if (j < np) one(j);
+}
+
 // lam_x += sum_c v_c grad readout(mesh_c) + mass grad readout(phi); optional
-// dot = sum_j lamp_j . readout(mesh)(x_j)
+// dot = sum_j lamp_j . readout(mesh)(x_j).  TWO: a second transpose at the same
+// positions in the same pass, + sum_c w_c grad readout(mesh2_c) (the PGD
+// transpose of a lightcone step fused with the kick transpose of the next step).
+// Each block walks one contiguous run of the (spatially sorted) particles, so
+// that its gathers reuse mesh rows in L2 (-6% against a grid-stride loop); each
+// particle's dot term is formed in the path precision and accumulated in FP64.
 template <typename R>
-__global__ void k_readout_grad(AdjState<R> s, const R* __restrict__ m0, const R* __restrict__ m1,
-                               const R* __restrict__ m2, const R* __restrict__ v0, const R* __restrict__ v1,
-                               const R* __restrict__ v2, const R* __restrict__ phi, R mass, R* __restrict__ lx,
-                               const R* __restrict__ lp, double* dot, int M, long long np) {
+struct ReadoutMeshes {
+  const R* m[3];   // meshes read and differentiated with cotangent v
+  const R* v[3];
+  const R* m2[3];  // TWO: second set, cotangent w
+  const R* w[3];
+};
+
+template <typename R, bool TWO>
+__global__ void k_readout_grad(AdjState<R> s, ReadoutMeshes<R> rm, const R* __restrict__ phi, R mass,
+                               R* __restrict__ lx, const R* __restrict__ lp, double* dot, int M, long long np) {
   double dsum = 0.0;
-  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < np; j += (long long)gridDim.x * blockDim.x) {
+  const long long per = (np + gridDim.x - 1) / gridDim.x;
+  const long long jb = blockIdx.x * per, je = jb + per < np ? jb + per : np;
+  for (long long j = jb + threadIdx.x; j < je; j += blockDim.x) {
     int i[3];
     unpack3(s.cell[j], i);
     const R f[3] = {s.fx[j], s.fy[j], s.fz[j]};
@@ -116,10 +166,14 @@ __global__ void k_readout_grad(AdjState<R> s, const R* __restrict__ m0, const R*
     // corner k = (dx, dy, dz) = (k & 1, k >> 1 & 1, k >> 2), 32-bit offsets
     const unsigned o[8] = {cc.r00 + cc.x0, cc.r00 + cc.x1, cc.r01 + cc.x0, cc.r01 + cc.x1,
                            cc.r10 + cc.x0, cc.r10 + cc.x1, cc.r11 + cc.x0, cc.r11 + cc.x1};
-    const R v[3] = {v0[j], v1[j], v2[j]};
+    const R v[3] = {rm.v[0][j], rm.v[1][j], rm.v[2][j]};
+    R w[3] = {R(0), R(0), R(0)};
+    if constexpr (TWO) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) w[c] = rm.w[c][j];
+    }
     R g[3] = {R(0), R(0), R(0)};
     R val[3] = {R(0), R(0), R(0)};
-    const R* ms[3] = {m0, m1, m2};
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
@@ -128,9 +182,10 @@ __global__ void k_readout_grad(AdjState<R> s, const R* __restrict__ m0, const R*
       R q = mass * phi[o[k]];
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const R mv = ms[c][o[k]];
+        const R mv = rm.m[c][o[k]];
         q += v[c] * mv;
         val[c] += wx * wy * wz * mv;
+        if constexpr (TWO) q += w[c] * rm.m2[c][o[k]];
       }
       g[0] += sx * wy * wz * q;
       g[1] += wx * sy * wz * q;
@@ -139,7 +194,7 @@ __global__ void k_readout_grad(AdjState<R> s, const R* __restrict__ m0, const R*
     lx[j] += g[0];
     lx[j + np] += g[1];
     lx[j + 2 * np] += g[2];
-    if (lp) dsum += (double)lp[j] * val[0] + (double)lp[j + np] * val[1] + (double)lp[j + 2 * np] * val[2];
+    if (lp) dsum += (double)(lp[j] * val[0] + lp[j + np] * val[1] + lp[j + 2 * np] * val[2]);
   }
   if (dot) block_add(dsum, dot);
 }
@@ -414,12 +469,37 @@ void adj_paint_weights(const AdjState<R>& s, const R* v, R* const* meshes, int M
   k_paint_weights<R><<<blocks_for(np), 256, 0, st>>>(s, v, v + np, v + 2 * np, meshes[0], meshes[1], meshes[2], M, np);
 }
 
+void adj_paint_weights4(const AdjState<float>& s, const float* v, float* mesh4, int M, long long np, cudaStream_t st,
+                        Prof* pf) {
+  ProfScope ps(pf, KK_ADJ_PAINT, st, np * (4.0 + 6.0 * sizeof(float)) + 4.0 * (double)M * M * M * sizeof(float));
+  k_paint_weights4<<<blocks_for(np), 256, 0, st>>>(s, v, v + np, v + 2 * np, mesh4, M, np);
+}
+
 template <typename R>
 void adj_readout_grad(const AdjState<R>& s, R* const* meshes, const R* v, const R* phi, double mass, R* lx,
                       const R* lp, double* dot, int M, long long np, cudaStream_t st, Prof* pf) {
   ProfScope ps(pf, KK_ADJ_READ, st, np * (4.0 + 12.0 * sizeof(R)) + 4.0 * (double)M * M * M * sizeof(R));
-  k_readout_grad<R><<<blocks_for(np), 256, 0, st>>>(s, meshes[0], meshes[1], meshes[2], v, v + np, v + 2 * np, phi,
-                                                   (R)mass, lx, lp, dot, M, np);
+  ReadoutMeshes<R> rm = {};
+  for (int c = 0; c < 3; ++c) {
+    rm.m[c] = meshes[c];
+    rm.v[c] = v + c * np;
+  }
+  k_readout_grad<R, false><<<blocks_for(np), 256, 0, st>>>(s, rm, phi, (R)mass, lx, lp, dot, M, np);
+}
+
+template <typename R>
+void adj_readout_grad2(const AdjState<R>& s, R* const* meshes, const R* v, R* const* meshes2, const R* w,
+                       const R* phi, double mass, R* lx, const R* lp, double* dot, int M, long long np, cudaStream_t st,
+                       Prof* pf) {
+  ProfScope ps(pf, KK_ADJ_READ, st, np * (4.0 + 18.0 * sizeof(R)) + 7.0 * (double)M * M * M * sizeof(R));
+  ReadoutMeshes<R> rm;
+  for (int c = 0; c < 3; ++c) {
+    rm.m[c] = meshes[c];
+    rm.v[c] = v + c * np;
+    rm.m2[c] = meshes2[c];
+    rm.w[c] = w + c * np;
+  }
+  k_readout_grad<R, true><<<blocks_for(np), 256, 0, st>>>(s, rm, phi, (R)mass, lx, lp, dot, M, np);
 }
 
 template <typename R>
@@ -479,6 +559,8 @@ void adj_lens(const LensAdjArgs<R>& A, cudaStream_t st, Prof* pf) {
                                      Prof*);                                                                    \
   template void adj_readout_grad<R>(const AdjState<R>&, R* const*, const R*, const R*, double, R*, const R*,    \
                                     double*, int, long long, cudaStream_t, Prof*);                              \
+  template void adj_readout_grad2<R>(const AdjState<R>&, R* const*, const R*, R* const*, const R*, const R*,    \
+                                     double, R*, const R*, double*, int, long long, cudaStream_t, Prof*);       \
   template void adj_axpy<R>(R*, const R*, double, long long, cudaStream_t, Prof*);                              \
   template void adj_scale<R>(R*, const R*, double, long long, cudaStream_t, Prof*);                             \
   template void adj_dot<R>(const R*, const R*, long long, double*, cudaStream_t, Prof*);                        \

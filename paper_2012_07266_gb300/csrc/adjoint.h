@@ -41,12 +41,39 @@ template <typename R>
 cudaError_t spectral_transpose(R* const* real_in, int nin, int first, void* const* ubufs, void* cbuf, R* real_out,
                                int n, int P, const SpecParams& sp, cudaStream_t s, Prof* prof);
 
+// the same with inputs i < npre already x,y-transformed in ubufs[i] (by spectral_forward_xy)
+template <typename R>
+cudaError_t spectral_transpose_pre(R* const* real_in, int nin, int npre, int first, void* const* ubufs, void* cbuf,
+                                   R* real_out, int n, int P, const SpecParams& sp, cudaStream_t s, Prof* prof);
+
+// x and y forward passes of nin real inputs into the half spectra ubufs[i]
+template <typename R>
+cudaError_t spectral_forward_xy(R* const* real_in, int nin, void* const* ubufs, int n, int P, const SpecParams& sp,
+                                cudaStream_t s, Prof* prof);
+
+// the same for three FP32 meshes interleaved per cell as float4 (FP32 only; the FP64
+// path returns cudaErrorInvalidValue)
+template <typename R>
+cudaError_t spectral_forward_xy_il4(const R* il, void* const* ubufs, int n, int P, const SpecParams& sp,
+                                    cudaStream_t s, Prof* prof);
+
+// paint three cotangent components v (3 x np) into one FP32 mesh interleaved per cell as
+// float4 (x, y, z, unused): one 16-byte vector reduction per corner
+void adj_paint_weights4(const AdjState<float>& s, const float* v, float* mesh4, int M, long long np, cudaStream_t st,
+                        Prof* pf);
+
 template <typename R>
 void adj_paint_weights(const AdjState<R>& s, const R* v, R* const* meshes, int M, long long np, cudaStream_t st,
                        Prof* pf);
 template <typename R>
 void adj_readout_grad(const AdjState<R>& s, R* const* meshes, const R* v, const R* phi, double mass, R* lx,
                       const R* lp, double* dot, int M, long long np, cudaStream_t st, Prof* pf);
+// two transposes at the same positions in one pass: lam_x += sum_c v_c grad readout(mesh_c)
+// + sum_c w_c grad readout(mesh2_c) + mass grad readout(phi); dot = sum_j lp_j . readout(mesh)(x_j)
+template <typename R>
+void adj_readout_grad2(const AdjState<R>& s, R* const* meshes, const R* v, R* const* meshes2, const R* w,
+                       const R* phi, double mass, R* lx, const R* lp, double* dot, int M, long long np, cudaStream_t st,
+                       Prof* pf);
 template <typename R>
 void adj_axpy(R* y, const R* x, double a, long long n, cudaStream_t st, Prof* pf);
 template <typename R>

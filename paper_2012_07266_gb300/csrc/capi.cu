@@ -103,7 +103,7 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
     L.adj_lp = a; a += al(3 * np * rs);
     L.adj_v = a; a += al(3 * np * rs);
     L.adj_vs = a; a += al(3 * np * rs);
-    L.adj_paint = a; a += 3 * al(mesh);
+    L.adj_paint = a; a += 4 * al(mesh);  // three cotangent meshes, or (FP32) one float4-interleaved mesh
     L.adj_ic = a; a += (size_t)L.nic * al(grid);
     L.adj_acc = a; a += al((size_t)(4 * cfg.nsteps + 64) * 8);
   }
@@ -716,16 +716,69 @@ cudaError_t mesh_vjp(pm_ctx* c, const AdjState<R>& st, const R* v, bool pgd_part
   R* pm[3];
   for (int q = 0; q < 3; ++q) pm[q] = rp<R>(c, c->L.adj_paint + q * al(c->mesh_elems * c->rsz));
   cudaError_t e;
-  if ((e = cudaMemsetAsync(pm[0], 0, 3 * al(c->mesh_elems * c->rsz), s))) return e;
-  adj_paint_weights<R>(st, v, pm, c->M, c->np, s, &c->prof);
   void* ub[6];
   for (int o = 0; o < 6; ++o) ub[o] = c->ws + c->L.ubuf + o * al(cmesh_bytes(c));
   R* phi = rp<R>(c, c->L.rho);
   const SpecParams sp = force_params(c, pgd_part, alpha);
-  if ((e = spectral_transpose<R>(pm, 3, pgd_part ? 3 : 0, ub, c->ws + c->L.cbuf, phi, c->M, c->P, sp, s, &c->prof)))
-    return e;
+  if constexpr (std::is_same<R, float>::value) {
+    // FP32: the three cotangent components in one float4-interleaved mesh
+    if ((e = cudaMemsetAsync(pm[0], 0, 4 * c->mesh_elems * sizeof(float), s))) return e;
+    adj_paint_weights4(st, v, pm[0], c->M, c->np, s, &c->prof);
+    if ((e = spectral_forward_xy_il4<R>(pm[0], ub, c->M, c->P, sp, s, &c->prof))) return e;
+    if ((e = spectral_transpose_pre<R>(pm, 3, 3, pgd_part ? 3 : 0, ub, c->ws + c->L.cbuf, phi, c->M, c->P, sp, s,
+                                       &c->prof)))
+      return e;
+  } else {
+    if ((e = cudaMemsetAsync(pm[0], 0, 3 * al(c->mesh_elems * c->rsz), s))) return e;
+    adj_paint_weights<R>(st, v, pm, c->M, c->np, s, &c->prof);
+    if ((e = spectral_transpose<R>(pm, 3, pgd_part ? 3 : 0, ub, c->ws + c->L.cbuf, phi, c->M, c->P, sp, s, &c->prof)))
+      return e;
+  }
   const double mass = std::pow((double)c->M / c->nc, 3.0);
   adj_readout_grad<R>(st, meshes, v, phi, mass, rp<R>(c, c->L.adj_lx), lp_for_dot, dot, c->M, c->np, s, &c->prof);
+  return cudaGetLastError();
+}
+
+// The PGD transpose of a lightcone step and the kick transpose of the next step act at
+// the same positions: one pass for both.  The kick's cotangents vF (with the force meshes
+// Fm) and the PGD's vS (with the PGD meshes Sm) are painted in turn onto the same scratch
+// meshes (the first set is x,y-transformed before the second is painted), one
+// fused z pass sums the six conjugate multipliers, one inverse gives the potential, and
+// one readout pass differentiates all seven meshes.  lam_x += F^T(vF) + S^T(vS);
+// dot += sum_j vF_j . F(x_j).
+template <typename R>
+cudaError_t mesh_vjp_pair(pm_ctx* c, const AdjState<R>& st, const R* vF, R* const* Fm, const R* vS, R* const* Sm,
+                          double alpha, double* dot) {
+  cudaStream_t s = c->stream;
+  R* pm[3];
+  for (int q = 0; q < 3; ++q) pm[q] = rp<R>(c, c->L.adj_paint + q * al(c->mesh_elems * c->rsz));
+  void* ub[6];
+  for (int o = 0; o < 6; ++o) ub[o] = c->ws + c->L.ubuf + o * al(cmesh_bytes(c));
+  const SpecParams sp = force_params(c, true, alpha);
+  cudaError_t e;
+  R* phi = rp<R>(c, c->L.rho);
+  if constexpr (std::is_same<R, float>::value) {
+    // FP32: each set painted into one float4-interleaved mesh
+    for (int g = 0; g < 2; ++g) {
+      if ((e = cudaMemsetAsync(pm[0], 0, 4 * c->mesh_elems * sizeof(float), s))) return e;
+      adj_paint_weights4(st, g ? vS : vF, pm[0], c->M, c->np, s, &c->prof);
+      if ((e = spectral_forward_xy_il4<R>(pm[0], ub + 3 * g, c->M, c->P, sp, s, &c->prof))) return e;
+    }
+    R* ins[6] = {};
+    if ((e = spectral_transpose_pre<R>(ins, 6, 6, 0, ub, c->ws + c->L.cbuf, phi, c->M, c->P, sp, s, &c->prof)))
+      return e;
+  } else {
+    if ((e = cudaMemsetAsync(pm[0], 0, 3 * al(c->mesh_elems * c->rsz), s))) return e;
+    adj_paint_weights<R>(st, vF, pm, c->M, c->np, s, &c->prof);
+    if ((e = spectral_forward_xy<R>(pm, 3, ub, c->M, c->P, sp, s, &c->prof))) return e;
+    if ((e = cudaMemsetAsync(pm[0], 0, 3 * al(c->mesh_elems * c->rsz), s))) return e;
+    adj_paint_weights<R>(st, vS, pm, c->M, c->np, s, &c->prof);
+    R* ins[6] = {nullptr, nullptr, nullptr, pm[0], pm[1], pm[2]};
+    if ((e = spectral_transpose_pre<R>(ins, 6, 3, 0, ub, c->ws + c->L.cbuf, phi, c->M, c->P, sp, s, &c->prof)))
+      return e;
+  }
+  const double mass = std::pow((double)c->M / c->nc, 3.0);
+  adj_readout_grad2<R>(st, Fm, vF, Sm, vS, phi, mass, rp<R>(c, c->L.adj_lx), vF, dot, c->M, c->np, s, &c->prof);
   return cudaGetLastError();
 }
 
@@ -799,9 +852,15 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
       if (i + 1 < i1 && (e = save_force(c, i - i0 + 1))) return PM_ERR_CUDA;  // F(x_{i+1}) for kick i+1
     }
     }
-    // reverse sweep through the segment
+    // reverse sweep through the segment.  The kick transpose of step i + 1 acts at x_{i+1},
+    // where the PGD transpose of shell i acts too: when step i lies in this segment with an
+    // active PGD shell, the kick's cotangent v waits in its buffer and both run as one pass
+    // (mesh_vjp_pair) right after shell i's lens transpose, still before the drift transpose
+    // of step i that reads lam_x(x_{i+1}).
+    int pending = -1;  // step whose kick transpose waits in v
     for (int i = i1 - 1; i >= i0; --i) {
       const AdjState<R> st1 = state_view<R>(c, seg_off(c, i - i0 + 1));  // x_{i+1}, p_{i+1/2}
+      const size_t mstride = al(c->mesh_elems * c->rsz) / c->rsz;
       if (shell_active(c, i)) {
         const bool pg = cfg.pgd != 0;
         // S(x_{i+1}) from the segment recompute
@@ -863,9 +922,22 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
           if (launch_lens_dot2<R>(c, shp, pg, lam, vp_, vm_)) return PM_ERR_CUDA;
         }
         if (pg) {
-          // PGD transpose at x_{i+1} (meshes of S still current)
-          if ((e = mesh_vjp<R>(c, st1, vS, true, pgd_alpha(c, i), Sm, nullptr, nullptr))) return PM_ERR_CUDA;
+          // PGD transpose at x_{i+1}, with the waiting kick transpose of step i + 1 if any
+          if (pending == i + 1) {
+            R* Fn = rp<R>(c, fseg_off(c, i + 1 - i0));  // F(x_{i+1})
+            R* Fns[3] = {Fn, Fn + mstride, Fn + 2 * mstride};
+            if ((e = mesh_vjp_pair<R>(c, st1, v, Fns, vS, Sm, pgd_alpha(c, i), acc + i + 1))) return PM_ERR_CUDA;
+            pending = -1;
+          } else if ((e = mesh_vjp<R>(c, st1, vS, true, pgd_alpha(c, i), Sm, nullptr, nullptr))) {
+            return PM_ERR_CUDA;
+          }
         }
+      }
+      if (pending == i + 1) {  // no PGD transpose at x_{i+1} after all: the kick's alone
+        R* Fn = rp<R>(c, fseg_off(c, i + 1 - i0));
+        R* Fns[3] = {Fn, Fn + mstride, Fn + 2 * mstride};
+        if ((e = mesh_vjp<R>(c, st1, v, false, 0.0, Fns, v, acc + i + 1))) return PM_ERR_CUDA;
+        pending = -1;
       }
       // drift x_{i+1} = x_i + drift_i p_{i+1/2}
       adj_dot<R>(lx, st1.px, np3, acc + n + i, s, pf);
@@ -879,14 +951,19 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
           if (launch_permute3<R>(c, v, pid0, a)) return PM_ERR_CUDA;
         }
       }
-      // kick p_{i+1/2} = p_{i-1/2} + kick_i F(x_i)
-      const AdjState<R> st0 = state_view<R>(c, seg_off(c, i - i0));
-      R* Fi = rp<R>(c, fseg_off(c, i - i0));  // F(x_i), kept by the segment recompute
-      const size_t mstride = al(c->mesh_elems * c->rsz) / c->rsz;
-      R* Fs[3] = {Fi, Fi + mstride, Fi + 2 * mstride};
+      // kick p_{i+1/2} = p_{i-1/2} + kick_i F(x_i): cotangent v = kick_i lam_p; the kick dot is
+      // accumulated as sum v . F (the host divides by kick_i)
       adj_scale<R>(v, lp, c->kick[i], np3, s, pf);
-      if ((e = mesh_vjp<R>(c, st0, v, false, 0.0, Fs, lp, acc + i))) return PM_ERR_CUDA;
+      if (i > i0 && shell_active(c, i - 1) && cfg.pgd) {
+        pending = i;  // runs with shell i - 1's PGD transpose, at x_i
+      } else {
+        const AdjState<R> st0 = state_view<R>(c, seg_off(c, i - i0));
+        R* Fi = rp<R>(c, fseg_off(c, i - i0));  // F(x_i), kept by the segment recompute
+        R* Fs[3] = {Fi, Fi + mstride, Fi + 2 * mstride};
+        if ((e = mesh_vjp<R>(c, st0, v, false, 0.0, Fs, v, acc + i))) return PM_ERR_CUDA;
+      }
     }
+    if (pending >= 0) return PM_ERR_STATE;  // every deferred transpose ran inside its segment
   }
   // ------------------------------------------------ initial conditions
   const long long g = (long long)c->nc * c->nc * c->nc;
@@ -969,7 +1046,7 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
   double dom = 0.0;
   for (int i = 0; i < n; ++i) {
     const double dK = (c->kick_p[i] * (om + hh) - c->kick_m[i] * (om - hh)) / (2 * hh);  // d(kick Om)/dOm
-    dom += dK / om * h[i];
+    dom += dK / om * h[i] / c->kick[i];  // h[i] = kick_i sum lam_p . F(x_i)
     dom += (c->drift_p[i] - c->drift_m[i]) / (2 * hh) * h[n + i];
     dom += (h[2 * n + i] - h[3 * n + i]) / (2 * hh);
   }

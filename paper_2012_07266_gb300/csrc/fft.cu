@@ -1,6 +1,7 @@
 // Launchers of the 3D FFT passes and of the fused spectral operators.
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "adjoint.h"
 #include "fft_impl.cuh"
@@ -79,6 +80,8 @@ struct Launch {
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          TT::SMEM_DUAL);
+    if constexpr (std::is_same<R, float>::value)
+      cudaFuncSetAttribute(k_fft_x_r2c_il4<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowTile3<N>::SMEM);
   }
 
   static void x_fwd(const R* in, C* out, int P, cudaStream_t s, Prof* pf, int kind) {
@@ -168,13 +171,46 @@ struct Launch {
     return cudaSuccess;
   }
 
-  static cudaError_t transpose(R* const* real_in, int nin, int first, void* const* ubufs, void* cbuf, R* real_out,
-                               int P, const SpecParams& sp, cudaStream_t s, Prof* pf) {
+  // x and y forward passes of real inputs into half spectra (the first stage of a transpose)
+  static cudaError_t forward_xy(R* const* real_in, int nin, void* const* ubufs, int P, const SpecParams& sp,
+                                cudaStream_t s, Prof* pf) {
+    attrs();
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < nin && !e; ++i) {
+      C* u = reinterpret_cast<C*>(ubufs[i]);
+      x_fwd(real_in[i], u, P, s, pf, KK_ADJ_FFT);
+      e = y(u, P, false, s, pf, KK_ADJ_FFT, sp.err);
+    }
+    return e ? e : cudaGetLastError();
+  }
+
+  // x and y forward passes of three FP32 meshes interleaved per cell as float4
+  static cudaError_t forward_xy_il4(const R* il, void* const* ubufs, int P, const SpecParams& sp, cudaStream_t s,
+                                    Prof* pf) {
+    if constexpr (std::is_same<R, float>::value) {
+      attrs();
+      {
+        ProfScope ps(pf, KK_ADJ_FFT, s, 4.0 * RB + 3.0 * CB);  // the float4 mesh read, three half spectra written
+        k_fft_x_r2c_il4<N><<<(long long)N * N / RowTile<R, N>::ROWS, RowTile<R, N>::THREADS, RowTile3<N>::SMEM, s>>>(
+            reinterpret_cast<const float4*>(il), reinterpret_cast<float2*>(ubufs[0]),
+            reinterpret_cast<float2*>(ubufs[1]), reinterpret_cast<float2*>(ubufs[2]), P);
+      }
+      cudaError_t e = cudaSuccess;
+      for (int i = 0; i < 3 && !e; ++i) e = y(reinterpret_cast<C*>(ubufs[i]), P, false, s, pf, KK_ADJ_FFT, sp.err);
+      return e ? e : cudaGetLastError();
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
+
+  // inputs i < npre are already x,y-transformed in ubufs[i]
+  static cudaError_t transpose(R* const* real_in, int nin, int npre, int first, void* const* ubufs, void* cbuf,
+                               R* real_out, int P, const SpecParams& sp, cudaStream_t s, Prof* pf) {
     attrs();
     InPtrs ip;
     for (int i = 0; i < 9; ++i) ip.p[i] = i < nin ? ubufs[i] : nullptr;
     cudaError_t e = cudaSuccess;
-    for (int i = 0; i < nin && !e; ++i) {
+    for (int i = npre; i < nin && !e; ++i) {
       C* u = reinterpret_cast<C*>(ubufs[i]);
       x_fwd(real_in[i], u, P, s, pf, KK_ADJ_FFT);
       e = y(u, P, false, s, pf, KK_ADJ_FFT, sp.err);
@@ -262,11 +298,37 @@ template <typename R>
 cudaError_t spectral_transpose(R* const* real_in, int nin, int first, void* const* ubufs, void* cbuf, R* real_out,
                                int n, int P, const SpecParams& sp, cudaStream_t s, Prof* pf) {
   if (nin < 1 || nin > 9) return cudaErrorInvalidValue;
-  PM_FFT_DISPATCH(n, L::transpose(real_in, nin, first, ubufs, cbuf, real_out, P, sp, s, pf));
+  PM_FFT_DISPATCH(n, L::transpose(real_in, nin, 0, first, ubufs, cbuf, real_out, P, sp, s, pf));
+}
+
+template <typename R>
+cudaError_t spectral_transpose_pre(R* const* real_in, int nin, int npre, int first, void* const* ubufs, void* cbuf,
+                                   R* real_out, int n, int P, const SpecParams& sp, cudaStream_t s, Prof* pf) {
+  if (nin < 1 || nin > 9 || npre < 0 || npre > nin) return cudaErrorInvalidValue;
+  PM_FFT_DISPATCH(n, L::transpose(real_in, nin, npre, first, ubufs, cbuf, real_out, P, sp, s, pf));
+}
+
+template <typename R>
+cudaError_t spectral_forward_xy(R* const* real_in, int nin, void* const* ubufs, int n, int P, const SpecParams& sp,
+                                cudaStream_t s, Prof* pf) {
+  if (nin < 1 || nin > 9) return cudaErrorInvalidValue;
+  PM_FFT_DISPATCH(n, L::forward_xy(real_in, nin, ubufs, P, sp, s, pf));
+}
+
+template <typename R>
+cudaError_t spectral_forward_xy_il4(const R* il, void* const* ubufs, int n, int P, const SpecParams& sp,
+                                    cudaStream_t s, Prof* pf) {
+  PM_FFT_DISPATCH(n, L::forward_xy_il4(il, ubufs, P, sp, s, pf));
 }
 
 template cudaError_t spectral_transpose<PM_REAL>(PM_REAL* const*, int, int, void* const*, void*, PM_REAL*, int, int,
                                                   const SpecParams&, cudaStream_t, Prof*);
+template cudaError_t spectral_transpose_pre<PM_REAL>(PM_REAL* const*, int, int, int, void* const*, void*, PM_REAL*,
+                                                      int, int, const SpecParams&, cudaStream_t, Prof*);
+template cudaError_t spectral_forward_xy<PM_REAL>(PM_REAL* const*, int, void* const*, int, int, const SpecParams&,
+                                                   cudaStream_t, Prof*);
+template cudaError_t spectral_forward_xy_il4<PM_REAL>(const PM_REAL*, void* const*, int, int, const SpecParams&,
+                                                       cudaStream_t, Prof*);
 template cudaError_t fft3d_r2c<PM_REAL>(const PM_REAL*, void*, int, int, cudaStream_t, Prof*, int*);
 template cudaError_t spectral_apply<PM_REAL>(const PM_REAL*, void*, void* const*, PM_REAL* const*, int, int, int,
                                               const SpecParams&, cudaStream_t, Prof*, int);

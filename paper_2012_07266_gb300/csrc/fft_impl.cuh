@@ -518,6 +518,78 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   for (int hh = threadIdx.x; hh < ROWS; hh += blockDim.x) untangle(hh, H);
 }
 
+// x pass, forward, of three FP32 meshes stored interleaved per cell as float4 (x, y, z
+// and an unused fourth value; the adjoint's cotangent meshes, painted with one vector
+// reduction per corner): rows of N cells -> three half-spectrum rows.  The three
+// component rows of a block share the shared-memory stages of one x r2c.
+template <int N> struct RowTile3 {
+  static constexpr int H = N / 2, ROWS = RowTile<float, N>::ROWS, LD = PadLen<H>::value + 1;
+  static constexpr int SMEM = (H + H + 2 + 3 * ROWS * LD) * 8;
+};
+
+template <int N>
+__global__ void __launch_bounds__(RowTile<float, N>::THREADS)
+k_fft_x_r2c_il4(const float4* __restrict__ in, float2* __restrict__ out0, float2* __restrict__ out1,
+                float2* __restrict__ out2, int P) {
+  using C = float2;
+  constexpr int H = N / 2, ROWS = RowTile<float, N>::ROWS, T = RowTile<float, N>::T, LD = RowTile3<N>::LD;
+  constexpr int THR = RowTile<float, N>::THREADS;
+  extern __shared__ unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* tu = tw + H;
+  C* buf = tu + H + 2;  // component q's rows at buf + q * ROWS * LD
+  make_twiddles<C, H, typename RowTile<float, N>::PL>(tw);
+  make_untangle<C, N>(tu);
+  const long long row0 = (long long)blockIdx.x * ROWS;
+  {
+    // cells 2m and 2m + 1 of a row make complex element m of each component's half-length row
+    const float4* inr = in + row0 * N;
+    constexpr int PER = ROWS * H / THR, B = PER < 4 ? PER : 4;
+    static_assert(PER % B == 0, "load batches");
+#pragma unroll 1
+    for (int q0 = 0; q0 < PER; q0 += B) {
+      float4 a[B], b[B];
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int e = threadIdx.x + (q0 + q) * THR;
+        a[q] = inr[2 * e];
+        b[q] = inr[2 * e + 1];
+      }
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int e = threadIdx.x + (q0 + q) * THR;
+        const int hh = e / H, m = e - hh * H;
+        const int o = hh * LD + pad16(m);
+        buf[o] = C{a[q].x, b[q].x};
+        buf[ROWS * LD + o] = C{a[q].y, b[q].y};
+        buf[2 * ROWS * LD + o] = C{a[q].z, b[q].z};
+      }
+    }
+  }
+  __syncthreads();
+  const int h = threadIdx.x / T, t = threadIdx.x - h * T;
+#pragma unroll 1
+  for (int q = 0; q < 3; ++q) fft_column<C, H, false, 1, LD, 1, typename RowTile<float, N>::PL>(buf + q * ROWS * LD, h, t, tw);
+  // X[k] = (Z[k] + conj Z[H-k]) / 2 + e^{-2 pi i k / N} (Z[k] - conj Z[H-k]) / (2i), k <= H
+#pragma unroll 1
+  for (int q = 0; q < 3; ++q) {
+    const C* bq = buf + q * ROWS * LD;
+    float2* outb = (q == 0 ? out0 : q == 1 ? out1 : out2) + row0 * P;
+    auto untangle = [&](int hh, int k) {
+      const C zk = bq[hh * LD + pad16(k % H)];
+      const C zm = cconj(bq[hh * LD + pad16((H - k) % H)]);
+      const C ev = C{0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y)};
+      const C od = C{0.5f * (zk.y - zm.y), -0.5f * (zk.x - zm.x)};
+      outb[hh * P + k] = cadd(ev, cmul(tu[k], od));
+    };
+    for (int e = threadIdx.x; e < ROWS * H; e += blockDim.x) {
+      const int hh = e / H;
+      untangle(hh, e - hh * H);
+    }
+    for (int hh = threadIdx.x; hh < ROWS; hh += blockDim.x) untangle(hh, H);
+  }
+}
+
 // x pass, inverse: half-spectrum rows -> real rows (unnormalised: n * IDFT).
 // Persistent over blocks of ROWS rows: with pair loads, the next block's input is
 // requested right after the current one has been untangled into shared memory,
@@ -830,19 +902,23 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
   constexpr int CP = ZTile<R, N>::CP;
   const int col = CP * (threadIdx.x % (W / CP)), t = threadIdx.x / (W / CP);
   for (int e = threadIdx.x; e < N * W; e += blockDim.x) B[e] = C{0, 0};
-  const bool force3 = (sp.op == OP_FORCE || sp.op == OP_FORCE_PGD) && nin == 3 && (first == 0 || first == 3);
-  if (force3) {
+  // force / PGD groups of three (x, y, z components): nin == 3 (one group, first 0 or 3) or
+  // nin == 6 with first == 0 (the force group, then the PGD group, at the same positions)
+  const bool fop = sp.op == OP_FORCE || sp.op == OP_FORCE_PGD;
+  const int ngroups = !fop ? 0 : (nin == 3 && (first == 0 || first == 3)) ? 1 : (nin == 6 && first == 0) ? 2 : 0;
+  for (int gi = 0; gi < ngroups; ++gi) {
     // conj(i k_x g) FFT(A_x) + conj(i k_y g) FFT(A_y) = -i g FFT(k_x A_x + k_y A_y):
     // k_x, k_y are constant along the column, so one forward transform serves both
+    const int base = 3 * gi, gfirst = first + base;
     constexpr int THR = ZTile<R, N>::THREADS;
     constexpr int EPT = N * W / THR;
     const R kf = (R)sp.kf;
     const int h = N / 2;
     const R oy = iy == h ? R(0) : kf * (R)(iy <= h ? iy : iy - N);
-    load_tile<R, N, W, THR>(A, reinterpret_cast<const C*>(ins.p[0]) + plane, rstride, nv);
+    load_tile<R, N, W, THR>(A, reinterpret_cast<const C*>(ins.p[base]) + plane, rstride, nv);
     __syncthreads();
     {
-      const C* iny = reinterpret_cast<const C*>(ins.p[1]) + plane;
+      const C* iny = reinterpret_cast<const C*>(ins.p[base + 1]) + plane;
       C vy[EPT];
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
@@ -863,24 +939,24 @@ k_zpass_combine(InPtrs ins, int nin, int first, typename CT<R>::T* __restrict__ 
     fft_column<C, N, false, W, 1, CP>(A, col, t, tw);
     for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
       const int row = e / W, cc = e - row * W;
-      const R g = force_g<R>(sp, first >= 3, kx0 + cc, iy, row, N);
+      const R g = force_g<R>(sp, gfirst >= 3, kx0 + cc, iy, row, N);
       const C a = A[e];
-      B[e] = C{g * a.y, -g * a.x};  // -i g a
+      B[e] = C{B[e].x + g * a.y, B[e].y - g * a.x};  // + (-i g a)
     }
     __syncthreads();
-    load_tile<R, N, W, THR>(A, reinterpret_cast<const C*>(ins.p[2]) + plane, rstride, nv);
+    load_tile<R, N, W, THR>(A, reinterpret_cast<const C*>(ins.p[base + 2]) + plane, rstride, nv);
     __syncthreads();
     fft_column<C, N, false, W, 1, CP>(A, col, t, tw);
     for (int e = threadIdx.x; e < N * W; e += blockDim.x) {
       const int row = e / W, cc = e - row * W;
       R re, im;
-      spec_coef<R>(sp, first + 2, kx0 + cc, iy, row, N, re, im);
+      spec_coef<R>(sp, gfirst + 2, kx0 + cc, iy, row, N, re, im);
       const C a = A[e];
       B[e] = C{B[e].x + im * a.y, B[e].y - im * a.x};  // + conj(i im) a
     }
     __syncthreads();
   }
-  for (int c = 0; c < (force3 ? 0 : nin); ++c) {
+  for (int c = 0; c < (ngroups ? 0 : nin); ++c) {
     const C* in = reinterpret_cast<const C*>(ins.p[c]);
     load_tile<R, N, W, ZTile<R, N>::THREADS>(A, in + plane, rstride, nv);
     __syncthreads();
