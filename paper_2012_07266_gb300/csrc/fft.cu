@@ -191,7 +191,7 @@ struct Launch {
       attrs();
       {
         ProfScope ps(pf, KK_ADJ_FFT, s, 4.0 * RB + 3.0 * CB);  // the float4 mesh read, three half spectra written
-        k_fft_x_r2c_il4<N><<<(long long)N * N / RowTile<R, N>::ROWS, RowTile<R, N>::THREADS, RowTile3<N>::SMEM, s>>>(
+        k_fft_x_r2c_il4<N><<<(long long)N * N / RowTile3<N>::ROWS, RowTile3<N>::THREADS, RowTile3<N>::SMEM, s>>>(
             reinterpret_cast<const float4*>(il), reinterpret_cast<float2*>(ubufs[0]),
             reinterpret_cast<float2*>(ubufs[1]), reinterpret_cast<float2*>(ubufs[2]), P);
       }

@@ -522,18 +522,23 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
 // and an unused fourth value; the adjoint's cotangent meshes, painted with one vector
 // reduction per corner): rows of N cells -> three half-spectrum rows.  The three
 // component rows of a block share the shared-memory stages of one x r2c.
+// A quarter of the x pass's rows per block (4 row triples at N = 512: 30 KB of shared
+// memory, 64 threads): more resident blocks hide the float4 loads (measured 4 ms per pm256
+// reverse sweep faster than 16 or 8 row triples).
 template <int N> struct RowTile3 {
-  static constexpr int H = N / 2, ROWS = RowTile<float, N>::ROWS, LD = PadLen<H>::value + 1;
+  static constexpr int H = N / 2, T = RowTile<float, N>::T, LD = PadLen<H>::value + 1;
+  static constexpr int ROWS = RowTile<float, N>::ROWS / 4 > 0 ? RowTile<float, N>::ROWS / 4 : 1;
+  static constexpr int THREADS = ROWS * T;
   static constexpr int SMEM = (H + H + 2 + 3 * ROWS * LD) * 8;
 };
 
 template <int N>
-__global__ void __launch_bounds__(RowTile<float, N>::THREADS)
+__global__ void __launch_bounds__(RowTile3<N>::THREADS)
 k_fft_x_r2c_il4(const float4* __restrict__ in, float2* __restrict__ out0, float2* __restrict__ out1,
                 float2* __restrict__ out2, int P) {
   using C = float2;
-  constexpr int H = N / 2, ROWS = RowTile<float, N>::ROWS, T = RowTile<float, N>::T, LD = RowTile3<N>::LD;
-  constexpr int THR = RowTile<float, N>::THREADS;
+  constexpr int H = N / 2, ROWS = RowTile3<N>::ROWS, T = RowTile3<N>::T, LD = RowTile3<N>::LD;
+  constexpr int THR = RowTile3<N>::THREADS;
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* tu = tw + H;
