@@ -56,6 +56,12 @@ def args_():
     ap.add_argument("--serve-requests", type=int, default=40)
     ap.add_argument("--cpu-single-thread", action="store_true",
                     help="also time the oracle baseline with one DFT thread")
+    ap.add_argument("--leg", default="forward", choices=["forward", "adjoint"],
+                    help="adjoint: each timed step is a forward run plus the reverse sweep (checkpoint "
+                         "every 4 unless the workload sets one; a profiling case)")
+    ap.add_argument("--large", action="store_true",
+                    help="also time the 512^3-particle workload: forward, and forward + reverse sweep "
+                         "checkpointed every 2 steps (269 GB of HBM)")
     return ap.parse_args()
 
 
@@ -66,7 +72,10 @@ def bench_workload(a):
         over["nc"] = a.nc
     if a.pgd is not None:
         over["pgd"] = a.pgd
-    return workload(a.workload, **over)
+    w = workload(a.workload, **over)
+    if getattr(a, "leg", "forward") == "adjoint" and not w.get("ckpt_every"):
+        w["ckpt_every"] = 4
+    return w
 
 
 def peaks():
@@ -343,8 +352,14 @@ def run_gpu(a, rank, world, local_rank):
     noise = torch.from_numpy(white_noise(w["nc"], rank_noise_seed(w, rank))).to(dev)
     npart, nsteps = w["nc"] ** 3, w["nsteps"]
 
+    lam = None
+    if a.leg == "adjoint":
+        lam = torch.ones((sim.n_zs, sim.npix, sim.npix), dtype=torch.float64, device=dev)
+
     def one():
         sim.run(noise)  # kappa_maps synchronises the stream
+        if lam is not None:
+            sim.vjp(lam)
 
     for _ in range(a.warmup):
         one()
@@ -432,6 +447,11 @@ def run_gpu(a, rank, world, local_rank):
             v1, dt1, smp1 = cpu_baseline_sample(w, workers=1)
             cpu["single_thread"] = {"value": v1, "cores": 1, "sample": smp1.describe(dt1)}
     extra = {} if (a.no_extra or world > 1) else extra_legs(a, w, dev, rank, ms)
+    ws_gb = sim.nbytes / 1e9
+    if a.large and world == 1:
+        del sim
+        torch.cuda.empty_cache()
+        extra["large"] = large_leg(dev)
     # whole-simulation roofline against the byte model of the path, R = 4 M^3, C = 8 M^2 (M/2 + 1):
     # every KDK step (paint, forward FFT, three inverse FFTs with the fused Poisson/gradient,
     # readout + kick, drift) 9 R + 20 C + 100 N_p; every lightcone step adds PGD (three inverse
@@ -454,8 +474,9 @@ def run_gpu(a, rank, world, local_rank):
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == PM_FP32 else "f64", "data": "synthetic",
             "config": {"workload": f"{a.workload}: {WORKLOAD_DESC.get(a.workload, '')}",
-                       "step": "one whole forward simulation (IC, all KDK steps, PGD, lightcone, kappa)",
-                       "l2": "inputs larger than L2 (workspace %.1f GB)" % (sim.nbytes / 1e9),
+                       "step": "one whole forward simulation (IC, all KDK steps, PGD, lightcone, kappa)"
+                               + (" and its reverse sweep (profiling leg)" if a.leg == "adjoint" else ""),
+                       "l2": "inputs larger than L2 (workspace %.1f GB)" % ws_gb,
                        "parallelism": f"replicas x{world}"},
             "clocks": clk, "e2e": e2e, "gpu_launches": launches, "roofline": roof,
             "cpu_baseline": cpu, "kernels": kern, "step_roofline_model": model,
@@ -517,6 +538,29 @@ def extra_legs(a, w, dev, rank, forward_ms):
 
     out["fwd_adjoint"], k = time_fwd_adj(nsteps)
     out["fwd_adjoint_ckpt4"], _ = time_fwd_adj(4)
+    # the differentiable workload at its own size (128^3 particles, 256^3 mesh, 20 steps, one
+    # 1024^2 map, checkpoint every 4): forward + reverse sweep per request
+    w3 = workload("pm128_vjp")
+    sim3 = Simulation(device=dev, stream=stream, precision=PM_FP32, **w3)
+    n3 = torch.from_numpy(white_noise(w3["nc"], w3["noise_seed"])).to(dev)
+    lam3 = sim3.run(n3).clone()
+    sim3.vjp(lam3)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    t3f = t3a = 0.0
+    for _ in range(3):
+        e0.record(stream)
+        sim3.run(n3)
+        e1.record(stream)
+        sim3.vjp(lam3)
+        e2.record(stream)
+        e2.synchronize()
+        t3f += e0.elapsed_time(e1) / 3
+        t3a += e0.elapsed_time(e2) / 3
+    out["config3_fwd_adjoint"] = {"workload": "pm128_vjp: " + WORKLOAD_DESC["pm128_vjp"] + ", checkpoint every 4",
+                                  "forward_ms": t3f, "forward_adjoint_ms": t3a, "workspace_gb": sim3.nbytes / 1e9,
+                                  "value": w3["nc"] ** 3 * w3["nsteps"] / (t3a * 1e-3), "unit": UNIT}
+    del sim3
+    torch.cuda.empty_cache()
     # forward-mode derivative along a noise direction (one whole run with the tangent)
     sim = Simulation(device=dev, stream=stream, precision=PM_FP32, **dict(w, jvp=1))
     d = torch.from_numpy(white_noise(w["nc"], w["noise_seed"] + 1000)).to(dev)
@@ -581,6 +625,48 @@ def extra_legs(a, w, dev, rank, forward_ms):
     out["serve"] = dict(st.summary(), requests=len(reqs), arrival_rate_hz=20.0,
                         adjoint_fraction=float(np.mean([r.adjoint for r in reqs])),
                         failed=sum(r.error is not None for r in reqs))
+    return out
+
+
+def large_leg(dev):
+    """The 512^3-particle workload (1024^3 mesh, 8 sources to z = 2.5, 4096^2 maps, PGD): one
+    timed forward after a warm-up run, then the forward + reverse sweep with a checkpoint every
+    2 steps if its workspace fits the device."""
+    import torch
+
+    from paper_2012_07266_gb300.api import PM_FP32, Simulation
+    from pm_inputs import white_noise, workload
+    w = workload("pm512")
+    out = {"workload": "pm512: " + WORKLOAD_DESC["pm512"]}
+    stream = torch.cuda.Stream(dev)
+    noise = torch.from_numpy(white_noise(w["nc"], w["noise_seed"])).to(dev)
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    sim = Simulation(device=dev, stream=stream, precision=PM_FP32, **w)
+    sim.run(noise)
+    e0.record(stream)
+    sim.run(noise)
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1)
+    out["forward"] = {"ms": t, "value": w["nc"] ** 3 * w["nsteps"] / (t * 1e-3), "unit": UNIT,
+                      "workspace_gb": sim.nbytes / 1e9}
+    del sim
+    torch.cuda.empty_cache()
+    try:
+        sim = Simulation(device=dev, stream=stream, precision=PM_FP32, **dict(w, ckpt_every=2))
+        lam = sim.run(noise).clone()
+        e0.record(stream)
+        sim.run(noise)
+        e1.record(stream)
+        sim.vjp(lam)
+        e2.record(stream)
+        e2.synchronize()
+        out["forward_adjoint_ckpt2"] = {"forward_ms": e0.elapsed_time(e1), "ms": e0.elapsed_time(e2),
+                                        "workspace_gb": sim.nbytes / 1e9}
+        del sim
+    except (RuntimeError, torch.cuda.OutOfMemoryError) as err:
+        out["forward_adjoint_ckpt2"] = {"failed": str(err).splitlines()[0][:200]}
+    torch.cuda.empty_cache()
     return out
 
 
