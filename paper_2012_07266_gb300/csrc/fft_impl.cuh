@@ -177,16 +177,27 @@ __device__ __forceinline__ constexpr int pad_step(int k) {
   else return -1;
 }
 
+// Identity load operator of a Stockham stage.
+struct NoOp {
+  template <typename C> __device__ __forceinline__ C operator()(int, int, C v) const { return v; }
+};
+
 // One Stockham stage over CP adjacent columns of N elements at
 // buf[row * RS + col * CS] (RS == 1: buf[pad16(row) + col * CS]); T = N / V
 // threads per column group, thread t handles V / RAD butterflies of each of
 // its CP columns with one set of twiddles.  Two adjacent FP32 columns
-// (CS == 1) move as one 16-byte shared-memory access.
-template <typename C, int N, int V, int RAD, bool INV, int NS, int RS, int CS, int CP>
-__device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
+// (CS == 1) move as one 16-byte shared-memory access.  The stage reads from
+// `src` (which may be `buf`), each element through op(row, column, value) --
+// the first stage of a transform applies an elementwise spectral operator as
+// it reads, instead of a separate pass over the tile -- and writes to `buf`.
+template <typename C, int N, int V, int RAD, bool INV, int NS, int RS, int CS, int CP, typename Op = NoOp>
+__device__ __forceinline__ void stage(const C* src, C* buf, int col, int t, const C* tw, const Op& op = Op{}) {
   constexpr bool VEC = CP == 2 && CS == 1 && RS != 1 && sizeof(C) == 8;
   auto at = [&](int row, int cc) -> C& {
     return RS == 1 ? buf[pad16(row) + (col + cc) * CS] : buf[row * RS + (col + cc) * CS];
+  };
+  auto at_src = [&](int row, int cc) -> const C& {
+    return RS == 1 ? src[pad16(row) + (col + cc) * CS] : src[row * RS + (col + cc) * CS];
   };
   constexpr int T = N / V;
   constexpr int NB = V / RAD;
@@ -199,19 +210,19 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
   for (int b = 0; b < NB; ++b) {
     const int j = t + b * T;
     if constexpr (RD_CONST && CP == 1) {
-      const C* rb = buf + pad16(j) + col * CS;
+      const C* rb = src + pad16(j) + col * CS;
 #pragma unroll
-      for (int k = 0; k < RAD; ++k) v[0][b][k] = rb[pad_step<NR, RAD, false, NS * RAD>(k)];
+      for (int k = 0; k < RAD; ++k) v[0][b][k] = op(j + k * NR, col, rb[pad_step<NR, RAD, false, NS * RAD>(k)]);
     } else {
 #pragma unroll
       for (int k = 0; k < RAD; ++k) {
         if constexpr (VEC) {
-          const float4 q = *reinterpret_cast<const float4*>(&at(j + k * NR, 0));
-          v[0][b][k] = C{q.x, q.y};
-          v[CP - 1][b][k] = C{q.z, q.w};
+          const float4 q = *reinterpret_cast<const float4*>(&at_src(j + k * NR, 0));
+          v[0][b][k] = op(j + k * NR, col, C{q.x, q.y});
+          v[CP - 1][b][k] = op(j + k * NR, col + CP - 1, C{q.z, q.w});
         } else {
 #pragma unroll
-          for (int cc = 0; cc < CP; ++cc) v[cc][b][k] = at(j + k * NR, cc);
+          for (int cc = 0; cc < CP; ++cc) v[cc][b][k] = op(j + k * NR, col + cc, at_src(j + k * NR, cc));
         }
       }
     }
@@ -260,16 +271,18 @@ __device__ __forceinline__ void stage(C* buf, int col, int t, const C* tw) {
   __syncthreads();
 }
 
-template <typename C, int N, int V, bool INV, int RS, int CS, int CP, int NS, int RAD, int... Rest>
-__device__ __forceinline__ void run_stages(C* buf, int col, int t, const C* tw) {
-  stage<C, N, V, RAD, INV, NS, RS, CS, CP>(buf, col, t, tw);
+template <typename C, int N, int V, bool INV, int RS, int CS, int CP, int NS, typename Op, int RAD, int... Rest>
+__device__ __forceinline__ void run_stages(const C* src, C* buf, int col, int t, const C* tw, const Op& op) {
+  stage<C, N, V, RAD, INV, NS, RS, CS, CP, Op>(src, buf, col, t, tw, op);
   if constexpr (sizeof...(Rest) > 0)
-    run_stages<C, N, V, INV, RS, CS, CP, NS * RAD, Rest...>(buf, col, t, NS > 1 ? tw + (RAD - 1) * NS : tw);
+    run_stages<C, N, V, INV, RS, CS, CP, NS * RAD, NoOp, Rest...>(buf, buf, col, t, NS > 1 ? tw + (RAD - 1) * NS : tw,
+                                                                  NoOp{});
 }
 
-template <typename C, int N, int V, bool INV, int RS, int CS, int CP, int... Rs>
-__device__ __forceinline__ void fft_column_impl(Radices<Rs...>, C* buf, int col, int t, const C* tw) {
-  run_stages<C, N, V, INV, RS, CS, CP, 1, Rs...>(buf, col, t, tw);
+template <typename C, int N, int V, bool INV, int RS, int CS, int CP, typename Op, int... Rs>
+__device__ __forceinline__ void fft_column_impl(Radices<Rs...>, const C* src, C* buf, int col, int t, const C* tw,
+                                                const Op& op) {
+  run_stages<C, N, V, INV, RS, CS, CP, 1, Op, Rs...>(src, buf, col, t, tw, op);
 }
 
 // In-place FFT of CP adjacent columns of length N held in shared memory:
@@ -277,7 +290,14 @@ __device__ __forceinline__ void fft_column_impl(Radices<Rs...>, C* buf, int col,
 // strides), with the radices and elements per thread of plan PL.
 template <typename C, int N, bool INV, int RS, int CS, int CP = 1, typename PL = Plan<N>>
 __device__ __forceinline__ void fft_column(C* buf, int col, int t, const C* tw) {
-  fft_column_impl<C, N, PL::V, INV, RS, CS, CP>(typename PL::Rad{}, buf, col, t, tw);
+  fft_column_impl<C, N, PL::V, INV, RS, CS, CP, NoOp>(typename PL::Rad{}, buf, buf, col, t, tw, NoOp{});
+}
+
+// The same transform of op(row, column, src element) into buf (src may be buf): an
+// elementwise spectral operator applied as the first stage reads.
+template <typename C, int N, bool INV, int RS, int CS, int CP = 1, typename PL = Plan<N>, typename Op>
+__device__ __forceinline__ void fft_column_from(const C* src, C* buf, int col, int t, const C* tw, const Op& op) {
+  fft_column_impl<C, N, PL::V, INV, RS, CS, CP, Op>(typename PL::Rad{}, src, buf, col, t, tw, op);
 }
 
 // Stage-major twiddles of the plan of N: for each stage with NS > 1, in order,

@@ -175,22 +175,22 @@ k_fft_cols_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ 
     }
     mbar_wait(bar(b), (it >> 1) & 1);  // completed phase: returns at once, acquires the tile per thread
     if constexpr (DUAL) {
-      // buf <- i k_x G, work2 <- i k_y G (rows are k_y, columns k_x)
+      // work2 <- IFFT_y(i k_y G), then buf <- IFFT_y(i k_x G) in place (rows are k_y,
+      // columns k_x): the factors are applied as each transform's first stage reads G
       constexpr int h = N / 2;
-      C* g = buf(b);
       const int kx0 = (ti % ntx) * W;
-      for (int e = threadIdx.x; e < N * W; e += TT::THREADS) {
-        const int row = e / W, ix = kx0 + (e - row * W);
-        const R ox = ix == h ? R(0) : kf * (R)(ix <= h ? ix : ix - N);
+      fft_column_from<C, N, INV, W, 1, CP>(buf(b), work2, col, t, tw, [&](int row, int, C a) {
         const R oy = row == h ? R(0) : kf * (R)(row <= h ? row : row - N);
-        const C a = g[e];
-        g[e] = C{-ox * a.y, ox * a.x};
-        work2[e] = C{-oy * a.y, oy * a.x};
-      }
-      __syncthreads();
-      fft_column<C, N, INV, W, 1, CP>(work2, col, t, tw);
+        return C{-oy * a.y, oy * a.x};
+      });
+      fft_column_from<C, N, INV, W, 1, CP>(buf(b), buf(b), col, t, tw, [&](int, int c, C a) {
+        const int ix = kx0 + c;
+        const R ox = ix == h ? R(0) : kf * (R)(ix <= h ? ix : ix - N);
+        return C{-ox * a.y, ox * a.x};
+      });  // ends with __syncthreads
+    } else {
+      fft_column<C, N, INV, W, 1, CP>(buf(b), col, t, tw);  // ends with __syncthreads
     }
-    fft_column<C, N, INV, W, 1, CP>(buf(b), col, t, tw);  // ends with __syncthreads
     fence_proxy_async();  // generic-proxy writes of the tile -> visible to the bulk store
     __syncthreads();
     if (leader) {
@@ -234,8 +234,8 @@ k_zpass_op_tma(const __grid_constant__ CUtensorMap in_map, const __grid_constant
                int npass, SpecParams sp, int* __restrict__ err) {
   using C = typename CT<R>::T;
   using ZT = ZTma<R, N>;
-  constexpr int W = ZT::W, CP = ZT::CP, THR = ZT::THREADS;
-  constexpr int EPT = N * W / THR;
+  constexpr int W = ZT::W, CP = ZT::CP;
+
   extern __shared__ __align__(1024) unsigned char smem_zt[];
   C* tw = reinterpret_cast<C*>(smem_zt);
   auto inbuf = [&](int b) { return reinterpret_cast<C*>(smem_zt + ZT::TW_BYTES + b * ZT::TILE_BYTES); };
@@ -300,7 +300,7 @@ k_zpass_op_tma(const __grid_constant__ CUtensorMap in_map, const __grid_constant
     const int fy = iy <= h ? iy : iy - N;
     fft_column<C, N, false, W, 1, CP>(A, col, t, tw);
     for (int pass = 0; pass < npass; ++pass) {
-      const bool zc = pass & 1;
+      const bool zc = pass & 1, pg = pass >= 2;
       const bool last = pass == npass - 1;
       C* T = last ? A : B;
       if (!last) {
@@ -308,26 +308,21 @@ k_zpass_op_tma(const __grid_constant__ CUtensorMap in_map, const __grid_constant
         if (leader) bulk_wait_read0();
         __syncthreads();
       }
-#pragma unroll
-      for (int q = 0; q < EPT; ++q) {
-        const int e = threadIdx.x + q * THR;
-        const int row = e / W, c = e - row * W, ix = kx0 + c;
-        C a = A[e];
-        if (!zc) {
-          const int fx = ix <= h ? ix : ix - N, fz = row <= h ? row : row - N;
-          const R k2 = kf * kf * (R)(fx * fx + fy * fy + fz * fz);
-          const R inv = k2 > R(0) ? R(1) / k2 : R(0);
-          const R f = pass == 0 ? (R)sp.scale * inv : (k2 > R(0) ? pratio * pgd_filter<R>(sp, k2, inv) : R(0));
-          a = C{f * a.x, f * a.y};
-          A[e] = a;
-          T[e] = a;
-        } else {
-          const R oz = row == h ? R(0) : kf * (R)(row <= h ? row : row - N);
-          T[e] = C{-oz * a.y, oz * a.x};  // i k_z a
-        }
-      }
-      __syncthreads();
-      fft_column<C, N, true, W, 1, CP>(T, col, t, tw);  // ends with __syncthreads
+      // this output's operator, applied as the inverse transform's first stage reads the
+      // spectrum A: g = (3/2) Om / k^2 (x,y group G and, times i k_z, F_z); with PGD the
+      // filter ratio on top (G_p, S_z).  A itself stays the forward spectrum.
+      auto op = [&](int row, int c, C a) {
+        const int ix = kx0 + c;
+        const int fx = ix <= h ? ix : ix - N, fz = row <= h ? row : row - N;
+        const R k2 = kf * kf * (R)(fx * fx + fy * fy + fz * fz);
+        const R inv = k2 > R(0) ? R(1) / k2 : R(0);
+        R f = (R)sp.scale * inv;
+        if (pg) f = k2 > R(0) ? f * pratio * pgd_filter<R>(sp, k2, inv) : R(0);
+        if (!zc) return C{f * a.x, f * a.y};
+        const R oz = row == h ? R(0) : kf * (R)fz;
+        return C{-oz * f * a.y, oz * f * a.x};  // i k_z f a
+      };
+      fft_column_from<C, N, true, W, 1, CP>(A, T, col, t, tw, op);  // ends with __syncthreads
       fence_proxy_async();
       __syncthreads();
       if (leader) store(&outs.m[pass], ti, T);
