@@ -82,6 +82,9 @@ struct Launch {
                          TT::SMEM_DUAL);
     if constexpr (std::is_same<R, float>::value)
       cudaFuncSetAttribute(k_fft_x_r2c_il4<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowTile3<N>::SMEM);
+    // an attribute this device refuses would otherwise surface as the error of an unrelated
+    // later launch check; a kernel that really needs it fails at its own launch
+    cudaGetLastError();
   }
 
   static void x_fwd(const R* in, C* out, int P, cudaStream_t s, Prof* pf, int kind) {
