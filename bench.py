@@ -676,7 +676,7 @@ def read_traffic(kernel, workload):
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    want = source_hash()
+    want = source_hash(kernel)
     for line in open(path):
         parts = line.split()
         if len(parts) == 4 and parts[0] == kernel and parts[1] == workload and parts[3] == want:
@@ -684,13 +684,23 @@ def read_traffic(kernel, workload):
     return None
 
 
-def source_hash():
+# the sources a kernel's device code and launch come from; a kernel not listed is
+# keyed on every source
+KERNEL_SOURCES = {
+    "fft_x_c2r": ("fft_impl.cuh", "fft.cu"),
+    "kick_drift_paint": ("particles.cu", "cic.cuh"),
+}
+
+
+def source_hash(kernel=None):
+    """SHA-1 prefix of the sources of `kernel` (all CUDA/C++ sources if None or unlisted):
+    a committed DRAM-traffic figure is used only while it still matches."""
     import hashlib
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2012_07266_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    files = KERNEL_SOURCES.get(kernel) or [f for f in os.listdir(d) if f.endswith((".cu", ".cuh", ".h", ".cpp"))]
+    for f in sorted(files):
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 
 
