@@ -100,41 +100,117 @@ __global__ void k_paint_weights(AdjState<R> s, const R* __restrict__ v0, const R
   if (j < np) one(j);
 }
 
-// the three cotangent components into one interleaved float4 mesh: per corner one
-// 16-byte reduction carries x, y, z (12 vector reductions per particle become 8; the
-// reductions' L2 throughput bounds this kernel)
-__global__ void __launch_bounds__(256) k_paint_weights4(AdjState<float> s, const float* __restrict__ v0,
-                                                        const float* __restrict__ v1, const float* __restrict__ v2,
-                                                        float* __restrict__ m4, int M, long long np) {
-  auto one = [&](long long j) {
-    int i[3];
-    unpack3(s.cell[j], i);
-    const Corners c = corners(M, i[0], i[1], i[2]);
+// the three cotangent components into one interleaved float4 mesh.  Each block
+// takes one contiguous run of PAINT4_RUN (spatially sorted) particles; when the
+// CIC footprint of the run fits a shared-memory tile of at most PAINT4_TILE
+// cells, the run is accumulated in the tile (three component planes) with
+// shared-memory atomics and the tile's non-zero cells are added to the mesh with
+// one 16-byte reduction each; otherwise (sparse runs, runs across the periodic
+// boundary) each corner of each particle is one 16-byte reduction (x, y, z in
+// one vector).  The mesh reductions' L2 throughput bounds the untiled form.
+constexpr int PAINT4_THREADS = 256, PAINT4_PPT = 4, PAINT4_RUN = PAINT4_THREADS * PAINT4_PPT;
+constexpr int PAINT4_TILE = 4000;  // 3 x 4 B per cell: 48 KB of static shared memory
+
+__device__ __forceinline__ void red_v4(float* p, float a, float b, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(d), "f"(0.f)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(PAINT4_THREADS) k_paint_weights4(AdjState<float> s, const float* __restrict__ v0,
+                                                                   const float* __restrict__ v1,
+                                                                   const float* __restrict__ v2,
+                                                                   float* __restrict__ m4, int M, long long np) {
+  __shared__ float tile[3][PAINT4_TILE];
+  __shared__ unsigned box[6];  // lo x, y, z; hi x, y, z
+  const long long jb = (long long)blockIdx.x * PAINT4_RUN;
+  const int tid = threadIdx.x;
+  if (tid < 3) box[tid] = 0xffffffffu;
+  else if (tid < 6) box[tid] = 0u;
+  int cell[PAINT4_PPT][3];
+  unsigned lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
+#pragma unroll
+  for (int q = 0; q < PAINT4_PPT; ++q) {
+    const long long j = jb + q * PAINT4_THREADS + tid;
+    if (j < np) {
+      unpack3(s.cell[j], cell[q]);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = min(lo[a], (unsigned)cell[q][a]);
+        hi[a] = max(hi[a], (unsigned)cell[q][a]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
+    hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
+  }
+  if ((tid & 31) == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(&box[a], lo[a]);
+      atomicMax(&box[3 + a], hi[a]);
+    }
+  }
+  __syncthreads();
+  const long long nrun = np - jb < PAINT4_RUN ? np - jb : PAINT4_RUN;
+  // tile extents: the run's cells plus the +1 CIC corner along each axis
+  const int ex = (int)(box[3] - box[0]) + 2, ey = (int)(box[4] - box[1]) + 2, ez = (int)(box[5] - box[2]) + 2;
+  const long long vol = (long long)ex * ey * ez;
+  const bool tiled = vol <= PAINT4_TILE;
+  if (tiled) {
+    for (int t = tid; t < vol; t += PAINT4_THREADS) tile[0][t] = tile[1][t] = tile[2][t] = 0.f;
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < PAINT4_PPT; ++q) {
+    const long long j = jb + q * PAINT4_THREADS + tid;
+    if (j >= np) continue;
     const float fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
     const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
     const float a = v0[j], b = v1[j], d = v2[j];
-    const unsigned rows[4] = {c.r00, c.r01, c.r10, c.r11};
     const float wr[4] = {gz * gy, gz * fy, fz * gy, fz * fy};
+    if (tiled) {
+      const int tx = cell[q][0] - (int)box[0], ty = cell[q][1] - (int)box[1], tz = cell[q][2] - (int)box[2];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+      for (int r = 0; r < 4; ++r) {
+        const int row = ((tz + (r >> 1)) * ey + ty + (r & 1)) * ex + tx;
 #pragma unroll
-      for (int dx = 0; dx < 2; ++dx) {
-        const float w = wr[q] * (dx ? fx : gx);
-        float* p = m4 + 4ull * (rows[q] + (dx ? c.x1 : c.x0));
-        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(w * a), "f"(w * b), "f"(w * d),
-                     "f"(0.f)
-                     : "memory");
+        for (int dx = 0; dx < 2; ++dx) {
+          const float w = wr[r] * (dx ? fx : gx);
+          atomicAdd(&tile[0][row + dx], w * a);
+          atomicAdd(&tile[1][row + dx], w * b);
+          atomicAdd(&tile[2][row + dx], w * d);
+        }
+      }
+    } else {
+      const Corners c = corners(M, cell[q][0], cell[q][1], cell[q][2]);
+      const unsigned rows[4] = {c.r00, c.r01, c.r10, c.r11};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const float w = wr[r] * (dx ? fx : gx);
+          red_v4(m4 + 4ull * (rows[r] + (dx ? c.x1 : c.x0)), w * a, w * b, w * d);
+        }
       }
     }
-  };
-  // two independent particles per iteration (overlapping their loads and reductions)
-  const long long S = (long long)gridDim.x * blockDim.x;
-  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  for (; j + S < np; j += 2 * S) {
-    one(j);
-    one(j + S);
   }
-  if (j < np) one(j);
+  if (!tiled) return;
+  __syncthreads();
+  // flush: tile cell (x, y, z) is mesh cell box_lo + (x, y, z), periodic (the +1 corner of the
+  // last cell of an axis is cell 0)
+  for (int t = tid; t < vol; t += PAINT4_THREADS) {
+    const float u0 = tile[0][t], u1 = tile[1][t], u2 = tile[2][t];
+    if (u0 == 0.f && u1 == 0.f && u2 == 0.f) continue;
+    const int x = t % ex, yz = t / ex, y = yz % ey, z = yz / ey;
+    int gx = (int)box[0] + x, gy = (int)box[1] + y, gz = (int)box[2] + z;
+    gx -= gx >= M ? M : 0;
+    gy -= gy >= M ? M : 0;
+    gz -= gz >= M ? M : 0;
+    red_v4(m4 + 4ull * (((unsigned)gz * M + gy) * (unsigned)M + gx), u0, u1, u2);
+  }
 }
 
 // lam_x += sum_c v_c grad readout(mesh_c) + mass grad readout(phi); optional
@@ -293,9 +369,9 @@ __global__ void k_lpt2_src_adj(const R* __restrict__ ls, const R* __restrict__ d
 // 256^3 adjoint).
 template <typename R>
 __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
-  const R cell_len = (R)A.cell_len;
-  const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
-  const R tan_half = (R)A.tan_half, margin = (R)A.margin;
+  const R cell_len = A.g.cell_len;
+  const R fov_half = A.g.fov_half, inv_dth = A.g.inv_dtheta;
+  const R tan_half = A.g.tan_half, margin = A.g.margin;
   // whole warps iterate together (warp-level replica culling, as in the forward)
   const int lane = threadIdx.x & 31;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -332,7 +408,7 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
         r[d] = ((R)gi[d] + f) * cell_len;
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2))) return;
+      if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2, A.g.lo2, A.g.hi2))) return;
       const R lim = r[2] * tan_half + margin;
       if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
       if (A.S0 && !have_s) {
@@ -361,9 +437,9 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
       R rc[3] = {r[0], r[1], r[2]};
       R dt = R(0), ddt = R(0);
       if (A.sub) {
-        const R t = interp_t<R>(A.tab_d1, A.tab_n, (R)A.tab_hinv, chi);
-        dt = (t - (R)A.d1_next) * (R)A.inv_gp_half;
-        ddt = interp_t<R>(A.tab_dd1, A.tab_n, (R)A.tab_hinv, chi) * (R)A.inv_gp_half;
+        const R t = interp_t<R>(A.tab_d1, A.tab_n, A.g.tab_hinv, chi);
+        dt = (t - A.d1_next_r) * A.inv_gp_half_r;
+        ddt = interp_t<R>(A.tab_dd1, A.tab_n, A.g.tab_hinv, chi) * A.inv_gp_half_r;
 #pragma unroll
         for (int d = 0; d < 3; ++d) rc[d] += pr[d] * dt * cell_len;
       }
@@ -382,33 +458,33 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
       const int iu = (int)fu0, iv = (int)fv0;
       const R fu = u - fu0, fv = v - fv0;
       const R cd = chic;
-      const R inva = interp_t<R>(A.tab_inva, A.tab_n, (R)A.tab_hinv, cd);
-      const R dinva = interp_t<R>(A.tab_dinva, A.tab_n, (R)A.tab_hinv, cd);
+      const R inva = interp_t<R>(A.tab_inva, A.tab_n, A.g.tab_hinv, cd);
+      const R dinva = interp_t<R>(A.tab_dinva, A.tab_n, A.g.tab_hinv, cd);
       R grc[3] = {0, 0, 0};
       for (int s = 0; s < A.nzs; ++s) {
         R w, dw;
         if (A.nz_mask >> s & 1u) {
           // source distribution: w = wpref q / (chi a), dw/dchi from q and dq/dchi
-          const R qv = interp_t<R>(A.qtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, cd);
+          const R qv = interp_t<R>(A.qtab + (size_t)s * A.tab_n, A.tab_n, A.g.tab_hinv, cd);
           if (!(qv > R(0))) continue;
-          const R dqv = interp_t<R>(A.dqtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, cd);
-          w = (R)A.wpref * qv / cd * inva;
-          dw = (R)A.wpref * ((dqv * cd - qv) / (cd * cd) * inva + qv / cd * dinva);
+          const R dqv = interp_t<R>(A.dqtab + (size_t)s * A.tab_n, A.tab_n, A.g.tab_hinv, cd);
+          w = A.wpref_r * qv / cd * inva;
+          dw = A.wpref_r * ((dqv * cd - qv) / (cd * cd) * inva + qv / cd * dinva);
         } else {
-          const R csd = (R)A.chi_s[s];
+          const R csd = A.chi_s_r[s];
           if (!(cd < csd)) continue;
           const R fr = R(1) / cd - R(1) / csd;
-          w = (R)A.wpref * fr * inva;
-          dw = (R)A.wpref * (-inva / (cd * cd) + fr * dinva);
+          w = A.wpref_r * fr * inva;
+          dw = A.wpref_r * (-inva / (cd * cd) + fr * dinva);
         }
-        const double* lam = A.lam + s * A.npix * A.npix;
+        const R* lam = A.lam + s * A.npix * A.npix;
         R Lw = 0, Lu = 0, Lv = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int du = k & 1, dv = k >> 1;
           const int jx = iu + du, jy = iv + dv;
           if (jx < 0 || jx >= A.npix || jy < 0 || jy >= A.npix) continue;
-          const R l = (R)lam[jy * A.npix + jx];
+          const R l = lam[jy * A.npix + jx];
           const R wu = du ? fu : R(1) - fu, wv = dv ? fv : R(1) - fv;
           Lw += l * wu * wv;
           Lu += l * (du ? R(1) : R(-1)) * wv;
@@ -444,8 +520,8 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
     };
     for (int base = 0; base < A.nrep; base += 32) {
       // replicas base..base+31 any particle of the warp may reach (warp-uniform ballot)
-      unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, (float)A.cell_len, (float)A.chi_lo2,
-                                    (float)A.chi_hi2, (float)A.tan_half, (float)A.margin);
+      unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, A.g.cull_cell_len, A.g.cull_lo2, A.g.cull_hi2,
+                                    A.g.cull_tan_half, A.g.cull_margin);
       if (!valid) live = 0u;
       while (live) {
         const int q = base + __ffs(live) - 1;
@@ -486,7 +562,8 @@ void adj_paint_weights(const AdjState<R>& s, const R* v, R* const* meshes, int M
 void adj_paint_weights4(const AdjState<float>& s, const float* v, float* mesh4, int M, long long np, cudaStream_t st,
                         Prof* pf) {
   ProfScope ps(pf, KK_ADJ_PAINT, st, np * (4.0 + 6.0 * sizeof(float)) + 4.0 * (double)M * M * M * sizeof(float));
-  k_paint_weights4<<<blocks_for(np), 256, 0, st>>>(s, v, v + np, v + 2 * np, mesh4, M, np);
+  const long long nb = (np + PAINT4_RUN - 1) / PAINT4_RUN;
+  if (nb > 0) k_paint_weights4<<<(unsigned)nb, PAINT4_THREADS, 0, st>>>(s, v, v + np, v + 2 * np, mesh4, M, np);
 }
 
 template <typename R>

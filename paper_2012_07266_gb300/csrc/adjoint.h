@@ -22,11 +22,13 @@ struct LensAdjArgs {
   int npix, nzs, sub;
   double chi_s[PM_MAX_ZS];
   double wpref, d1_next, inv_gp_half, tab_hinv;
+  R chi_s_r[PM_MAX_ZS], wpref_r, d1_next_r, inv_gp_half_r;  // the same rounded to R on the host
+  GeomMirrors<R> g;                                          // the geometry scalars rounded to R
   int tab_n;
   const R *tab_d1, *tab_dd1, *tab_inva, *tab_dinva;  // path precision
   unsigned nz_mask;         // bit s: source s is a distribution n(z)
   const R *qtab, *dqtab;    // its q(chi) and dq/dchi, n_zs x tab_n
-  const double* lam;  // dL/dkappa, n_zs * npix^2
+  const R* lam;       // dL/dkappa, n_zs * npix^2, in the path precision
   R* lx;              // d/dx accumulators (cells), 3 * np
   R* lp;              // d/dp accumulators (cells), 3 * np
   R* vS;              // d/dS out (cells), 3 * np, or null
@@ -102,8 +104,9 @@ struct LensDotVar {
 };
 // lens kernel in "dot" mode for two cosmologies on the selection (shell bounds,
 // replicas) of `sel`: a.acc += sum lam * (map increment under a), same for b
+// (lam in the path precision)
 template <typename R>
-cudaError_t launch_lens_dot2(pm_ctx* c, const LensShell& sel, int use_pgd, const double* lam, const LensDotVar& a,
+cudaError_t launch_lens_dot2(pm_ctx* c, const LensShell& sel, int use_pgd, const R* lam, const LensDotVar& a,
                              const LensDotVar& b);
 
 // ---------------------------------------------------------- tangent-linear (jvp.cu)

@@ -105,6 +105,7 @@ void plan_layout(const pm_config& cfg, Layout& L, int& P, int& Pc) {
     L.adj_vs = a; a += al(3 * np * rs);
     L.adj_paint = a; a += 4 * al(mesh);  // three cotangent meshes, or (FP32) one float4-interleaved mesh
     L.adj_ic = a; a += (size_t)L.nic * al(grid);
+    L.adj_lam = a; a += rs == 4 ? al((size_t)cfg.n_zs * cfg.map_npix * cfg.map_npix * 4) : 0;
     L.adj_acc = a; a += al((size_t)(4 * cfg.nsteps + 64) * 8);
   }
   if (cfg.jvp) {
@@ -674,25 +675,7 @@ size_t seg_off(pm_ctx* c, int j) { return c->L.adj_seg + (size_t)j * c->L.state_
 size_t fseg_off(pm_ctx* c, int j) { return c->L.adj_fseg + (size_t)j * 3 * al(c->mesh_elems * c->rsz); }
 size_t sseg_off(pm_ctx* c, int j) { return c->L.adj_sseg + (size_t)j * 3 * al(c->mesh_elems * c->rsz); }
 
-// keep the current force meshes as segment entry j
-cudaError_t save_force(pm_ctx* c, int j) {
-  const size_t m = c->mesh_elems * c->rsz;
-  cudaError_t e = cudaSuccess;
-  for (int q = 0; q < 3 && !e; ++q)
-    e = cudaMemcpyAsync(c->ws + fseg_off(c, j) + q * al(m), c->ws + c->L.fmesh + q * m, m, cudaMemcpyDeviceToDevice,
-                        c->stream);
-  return e;
-}
 size_t ckpt_off(pm_ctx* c, int j) { return c->L.adj_ckpt + (size_t)j * c->L.state_bytes; }
-
-template <typename R>
-cudaError_t force_at_working(pm_ctx* c, bool pgd, double alpha) {
-  R* rho = rp<R>(c, c->L.rho);
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, c->stream))) return e;
-  if ((e = launch_paint<R>(c, rho))) return e;
-  return force_from_rho<R>(c, pgd, alpha);
-}
 
 SpecParams force_params(pm_ctx* c, bool pgd, double alpha) {
   SpecParams sp = {};
@@ -814,6 +797,16 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
   if ((e = cudaMemsetAsync(lp, 0, np3 * c->rsz, s))) return PM_ERR_CUDA;
   if ((e = cudaMemsetAsync(acc, 0, (size_t)(4 * n + 64) * 8, s))) return PM_ERR_CUDA;
   for (int q = 0; q < cfg.n_zs; ++q) adj_dsum(lam + q * npix2, npix2, acc + 4 * n + q, s, pf);
+  // the projection transposes read lam in the path precision (FP32: rounded once here
+  // instead of converted at every read)
+  const R* lam_r;
+  if constexpr (std::is_same<R, float>::value) {
+    float* l32 = rp<float>(c, c->L.adj_lam);
+    if ((e = launch_convert_in<float>(lam, l32, cfg.n_zs * npix2, s, pf))) return PM_ERR_CUDA;
+    lam_r = l32;
+  } else {
+    lam_r = lam;
+  }
   R* F = rp<R>(c, c->L.fmesh);
   R* Fm[3] = {F, F + c->mesh_elems, F + 2 * c->mesh_elems};
   const double vp = std::pow(cfg.box / c->nc, 3.0);
@@ -835,21 +828,30 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
     }
     // recompute the segment forward from its checkpoint, keeping every state
     // (resident mode: the forward already kept them)
+    // The force meshes F(x_i) are written straight into their segment slots (the force
+    // evaluation's output pointers), where the next kick reads them: no copies.
     if (!resident) {
     if ((e = load_state(c, ckpt_off(c, seg)))) return PM_ERR_CUDA;
-    if ((e = force_at_working<R>(c, false, 0.0))) return PM_ERR_CUDA;
+    {
+      R* rho = rp<R>(c, c->L.rho);
+      if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, s))) return PM_ERR_CUDA;
+      if ((e = launch_paint<R>(c, rho))) return PM_ERR_CUDA;
+      if ((e = force_from_rho<R>(c, false, 0.0, 0, fseg_off(c, 0)))) return PM_ERR_CUDA;
+      c->f_at = fseg_off(c, 0);
+    }
     if ((e = save_state(c, seg_off(c, 0)))) return PM_ERR_CUDA;
-    if ((e = save_force(c, 0))) return PM_ERR_CUDA;
     for (int i = i0; i < i1; ++i) {
       R* rho = rp<R>(c, c->L.rho);
       if ((e = cudaMemsetAsync(rho, 0, c->mesh_elems * c->rsz, s))) return PM_ERR_CUDA;
-      if ((e = launch_kdk_paint<R>(c, rho, c->kick[i], c->drift[i]))) return PM_ERR_CUDA;
-      // lens steps with PGD: S(x_{i+1}) comes with the force, kept for the reverse sweep
+      if ((e = launch_kdk_paint<R>(c, rho, c->kick[i], c->drift[i]))) return PM_ERR_CUDA;  // reads F at f_at
+      // lens steps with PGD: S(x_{i+1}) comes with the force, kept for the reverse sweep;
+      // F(x_{i+1}) for kick i + 1 goes to slot i + 1 of the segment
       const bool pg_i = cfg.pgd && shell_active(c, i);
-      if ((e = force_from_rho<R>(c, pg_i, pg_i ? pgd_alpha(c, i) : 0.0, pg_i ? sseg_off(c, i - i0) : 0)))
+      const size_t f_off = i + 1 < i1 ? fseg_off(c, i - i0 + 1) : 0;
+      if ((e = force_from_rho<R>(c, pg_i, pg_i ? pgd_alpha(c, i) : 0.0, pg_i ? sseg_off(c, i - i0) : 0, f_off)))
         return PM_ERR_CUDA;
+      c->f_at = f_off;
       if ((e = save_state(c, seg_off(c, i - i0 + 1)))) return PM_ERR_CUDA;
-      if (i + 1 < i1 && (e = save_force(c, i - i0 + 1))) return PM_ERR_CUDA;  // F(x_{i+1}) for kick i+1
     }
     }
     // reverse sweep through the segment.  The kick transpose of step i + 1 acts at x_{i+1},
@@ -893,6 +895,12 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
         A.d1_next = sh.d1_next;
         A.inv_gp_half = 1.0 / sh.gp_half;
         A.tab_hinv = 1.0 / c->chi_tab_h;
+        for (int q = 0; q < PM_MAX_ZS; ++q) A.chi_s_r[q] = (R)A.chi_s[q];
+        A.wpref_r = (R)A.wpref;
+        A.d1_next_r = (R)A.d1_next;
+        A.inv_gp_half_r = (R)A.inv_gp_half;
+        A.g = geom_mirrors<R>(A.cell_len, A.chi_lo2, A.chi_hi2, A.fov_half, A.inv_dtheta, A.tan_half, A.margin,
+                              A.tab_hinv);
         A.tab_n = kChiTab;
         A.tab_d1 = chi_table<R>(c, T_D1);
         A.tab_dd1 = chi_table<R>(c, T_DD1);
@@ -901,7 +909,7 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
         A.nz_mask = c->nz_mask;
         A.qtab = qtable<R>(c, Q_CENTRAL);
         A.dqtab = qtable<R>(c, Q_DERIV);
-        A.lam = lam;
+        A.lam = lam_r;
         A.lx = lx;
         A.lp = lp;
         A.vS = pg ? vS : nullptr;
@@ -919,7 +927,7 @@ pm_status do_vjp(pm_ctx* c, const double* lam, double* d_noise_out, double* h_pa
                                   acc + 2 * n + i};
           const LensDotVar vm_ = {T_D1M, T_INVAM, Q_MINUS, c->chi_s_m.data(), wpref_m, shm.d1_next, shm.gp_half,
                                   acc + 3 * n + i};
-          if (launch_lens_dot2<R>(c, shp, pg, lam, vp_, vm_)) return PM_ERR_CUDA;
+          if (launch_lens_dot2<R>(c, shp, pg, lam_r, vp_, vm_)) return PM_ERR_CUDA;
         }
         if (pg) {
           // PGD transpose at x_{i+1}, with the waiting kick transpose of step i + 1 if any

@@ -174,6 +174,8 @@ struct LensTanArgs {
   int npix, nzs, sub;
   double chi_s[PM_MAX_ZS];
   double wpref, d1_next, inv_gp_half, tab_hinv;
+  R chi_s_r[PM_MAX_ZS], wpref_r, d1_next_r, inv_gp_half_r;  // the same rounded to R on the host
+  GeomMirrors<R> g;                                          // the geometry scalars rounded to R
   int tab_n;
   const R *tab_d1, *tab_dd1, *tab_inva, *tab_dinva;
   unsigned nz_mask;       // bit s: source s is a distribution n(z)
@@ -187,9 +189,9 @@ struct LensTanArgs {
 // d(w cw_k) = dw/dchi_c dchi_c cw_k + w d cw_k, deposited on the same pixels.
 template <typename R>
 __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
-  const R cell_len = (R)A.cell_len;
-  const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
-  const R tan_half = (R)A.tan_half, margin = (R)A.margin;
+  const R cell_len = A.g.cell_len;
+  const R fov_half = A.g.fov_half, inv_dth = A.g.inv_dtheta;
+  const R tan_half = A.g.tan_half, margin = A.g.margin;
   const R* fr = reinterpret_cast<const R*>(A.st.frac);
   const R* mo = reinterpret_cast<const R*>(A.st.mom);
   const int lane = threadIdx.x & 31;
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
         dpr[d] = sg[d] * pick3(ax, tp0, tp1, tp2);
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2))) return;
+      if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2, A.g.lo2, A.g.hi2))) return;
       const R lim = r[2] * tan_half + margin;
       if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
       if (A.S0 && !have_s) {
@@ -255,9 +257,9 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
       for (int d = 0; d < 3; ++d) { rc[d] = r[d]; drc[d] = dr[d]; }
       if (A.sub) {
         const R chi = sqrt(chi2);
-        const R t = interp_tab<R>(A.tab_d1, A.tab_n, (R)A.tab_hinv, chi);
-        const R dt = (t - (R)A.d1_next) * (R)A.inv_gp_half * cell_len;
-        const R ddt = interp_tab<R>(A.tab_dd1, A.tab_n, (R)A.tab_hinv, chi) * (R)A.inv_gp_half * cell_len;
+        const R t = interp_tab<R>(A.tab_d1, A.tab_n, A.g.tab_hinv, chi);
+        const R dt = (t - A.d1_next_r) * A.inv_gp_half_r * cell_len;
+        const R ddt = interp_tab<R>(A.tab_dd1, A.tab_n, A.g.tab_hinv, chi) * A.inv_gp_half_r * cell_len;
         const R dchi = (r[0] * dr[0] + r[1] * dr[1] + r[2] * dr[2]) / chi;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -286,23 +288,23 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
       const R fu0 = floor(u), fv0 = floor(v);
       const int iu = (int)fu0, iv = (int)fv0;
       const R fu = u - fu0, fv = v - fv0;
-      const R inva = interp_tab<R>(A.tab_inva, A.tab_n, (R)A.tab_hinv, chic);
-      const R dinva = interp_tab<R>(A.tab_dinva, A.tab_n, (R)A.tab_hinv, chic);
+      const R inva = interp_tab<R>(A.tab_inva, A.tab_n, A.g.tab_hinv, chic);
+      const R dinva = interp_tab<R>(A.tab_dinva, A.tab_n, A.g.tab_hinv, chic);
       for (int s = 0; s < A.nzs; ++s) {
         R w, dw;
         if (A.nz_mask >> s & 1u) {
           // source distribution: w = wpref q / (chi a)
-          const R qv = interp_tab<R>(A.qtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, chic);
+          const R qv = interp_tab<R>(A.qtab + (size_t)s * A.tab_n, A.tab_n, A.g.tab_hinv, chic);
           if (!(qv > R(0))) continue;
-          const R dqv = interp_tab<R>(A.dqtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, chic);
-          w = (R)A.wpref * qv / chic * inva;
-          dw = (R)A.wpref * ((dqv * chic - qv) / (chic * chic) * inva + qv / chic * dinva) * dchic;
+          const R dqv = interp_tab<R>(A.dqtab + (size_t)s * A.tab_n, A.tab_n, A.g.tab_hinv, chic);
+          w = A.wpref_r * qv / chic * inva;
+          dw = A.wpref_r * ((dqv * chic - qv) / (chic * chic) * inva + qv / chic * dinva) * dchic;
         } else {
-          const R csd = (R)A.chi_s[s];
+          const R csd = A.chi_s_r[s];
           if (!(chic < csd)) continue;
           const R fq = R(1) / chic - R(1) / csd;
-          w = (R)A.wpref * fq * inva;
-          dw = (R)A.wpref * (-inva / (chic * chic) + fq * dinva) * dchic;
+          w = A.wpref_r * fq * inva;
+          dw = A.wpref_r * (-inva / (chic * chic) + fq * dinva) * dchic;
         }
         const int off = s * A.npix * A.npix;
 #pragma unroll
@@ -312,14 +314,14 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
           if (jx < 0 || jx >= A.npix || jy < 0 || jy >= A.npix) continue;
           const R wu = ku ? fu : R(1) - fu, wv = kv ? fv : R(1) - fv;
           const R dwu = ku ? du : -du, dwv = kv ? dv : -dv;
-          atomicAdd(A.dmaps + off + jy * A.npix + jx, (double)(dw * wu * wv + w * (dwu * wv + wu * dwv)));
+          atomicAdd(A.dmaps + off + jy * A.npix + jx, to_f64(dw * wu * wv + w * (dwu * wv + wu * dwv)));
         }
       }
     };
     for (int base = 0; base < A.nrep; base += 32) {
       // replicas base..base+31 any particle of the warp may reach (warp-uniform ballot)
-      unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, (float)A.cell_len, (float)A.chi_lo2,
-                                    (float)A.chi_hi2, (float)A.tan_half, (float)A.margin);
+      unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, A.g.cull_cell_len, A.g.cull_lo2, A.g.cull_hi2,
+                                    A.g.cull_tan_half, A.g.cull_margin);
       if (!valid) live = 0u;
       while (live) {
         const int q = base + __ffs(live) - 1;
@@ -419,6 +421,12 @@ cudaError_t launch_tan_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
   A.d1_next = sh.d1_next;
   A.inv_gp_half = 1.0 / sh.gp_half;
   A.tab_hinv = 1.0 / c->chi_tab_h;
+  for (int s = 0; s < PM_MAX_ZS; ++s) A.chi_s_r[s] = (R)A.chi_s[s];
+  A.wpref_r = (R)A.wpref;
+  A.d1_next_r = (R)A.d1_next;
+  A.inv_gp_half_r = (R)A.inv_gp_half;
+  A.g = geom_mirrors<R>(A.cell_len, A.chi_lo2, A.chi_hi2, A.fov_half, A.inv_dtheta, A.tan_half, A.margin,
+                        A.tab_hinv);
   A.tab_n = kChiTab;
   A.tab_d1 = chi_table<R>(c, T_D1);
   A.tab_dd1 = chi_table<R>(c, T_DD1);

@@ -26,6 +26,7 @@ struct LensVar {
   double chi_s[PM_MAX_ZS];
   double wpref;       // (3/2) Om (H0/c)^2 V_p / Omega_pix
   double d1_next, inv_gp_half;
+  R chi_s_r[PM_MAX_ZS], wpref_r, d1_next_r, inv_gp_half_r;  // the same rounded to R on the host
   const R* qtab;      // q(chi) of the n(z) sources, n_zs x tab_n (sources in nz_mask)
   double* acc;
 };
@@ -50,7 +51,8 @@ struct LensArgs {
   double* maps;
   int* flag;
   unsigned long long* gathers;  // count of PGD gathers (forward projection), or null
-  const double* lam;  // when set: accumulate sum(lam * increment) into var[v].acc instead of the maps
+  const R* lam;       // when set: accumulate sum(lam * increment) into var[v].acc instead of the maps
+  GeomMirrors<R> g;   // the geometry scalars above rounded to R (and FP32 for the culling)
   int nrep;
   Replica rep[kMaxReplicas];
 };
@@ -104,9 +106,9 @@ __device__ __forceinline__ R gather3(const R* __restrict__ m, int M, int ix, int
 // shell selection and the PGD gather (NV = 2: the Omega_m +/- h dot products).
 template <typename R, int NV>
 __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
-  const R cell_len = (R)A.cell_len;
-  const R fov_half = (R)A.fov_half, inv_dth = (R)A.inv_dtheta;
-  const R tan_half = (R)A.tan_half, margin = (R)A.margin;
+  const R cell_len = A.g.cell_len;
+  const R fov_half = A.g.fov_half, inv_dth = A.g.inv_dtheta;
+  const R tan_half = A.g.tan_half, margin = A.g.margin;
   R dot[NV];
 #pragma unroll
   for (int vi = 0; vi < NV; ++vi) dot[vi] = R(0);
@@ -151,7 +153,7 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         sr[d] = sg * pick3(ax, cs0, cs1, cs2);
       }
       const R chi2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
-      if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2))) return;
+      if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2, A.g.lo2, A.g.hi2))) return;
       // outside the field of view by more than the displacement margin: no weight on the map
       const R lim = r[2] * tan_half + margin;
       if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
@@ -173,8 +175,8 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         const LensVar<R>& V = A.var[vi];
         R q[3] = {r[0], r[1], r[2]};
         if (A.sub) {
-          const R t = interp<R>(V.tab_d1, A.tab_n, (R)A.tab_hinv, chi);
-          const R dt = (t - (R)V.d1_next) * (R)V.inv_gp_half * cell_len;
+          const R t = interp<R>(V.tab_d1, A.tab_n, A.g.tab_hinv, chi);
+          const R dt = (t - V.d1_next_r) * V.inv_gp_half_r * cell_len;
 #pragma unroll
           for (int d = 0; d < 3; ++d) q[d] += pr[d] * dt;
         }
@@ -196,17 +198,17 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
         const int iu = (int)fu0, iv = (int)fv0;
         const R fu = u - fu0, fv = v - fv0;
         // Born weight in the path's precision, map accumulation in FP64
-        const R inva = interp<R>(V.tab_inva, A.tab_n, (R)A.tab_hinv, chic);
+        const R inva = interp<R>(V.tab_inva, A.tab_n, A.g.tab_hinv, chic);
         const R cw[4] = {(R(1) - fu) * (R(1) - fv), fu * (R(1) - fv), (R(1) - fu) * fv, fu * fv};
-        const R wk = (R)V.wpref * inva / chic;
+        const R wk = V.wpref_r * inva / chic;
         for (int s = 0; s < A.nzs; ++s) {
           R w;
           if (A.nz_mask >> s & 1u) {  // source distribution: w = wpref q(chi_c) / (chi_c a)
-            const R qv = interp<R>(V.qtab + (size_t)s * A.tab_n, A.tab_n, (R)A.tab_hinv, chic);
+            const R qv = interp<R>(V.qtab + (size_t)s * A.tab_n, A.tab_n, A.g.tab_hinv, chic);
             if (!(qv > R(0))) continue;
             w = wk * qv;
           } else {  // source plane at chi_s
-            const R cs_ = (R)V.chi_s[s];
+            const R cs_ = V.chi_s_r[s];
             if (!(chic < cs_)) continue;
             w = wk * (cs_ - chic) / cs_;
           }
@@ -216,8 +218,8 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
             const int jx = iu + (k & 1), jy = iv + (k >> 1);
             if (jx >= 0 && jx < A.npix && jy >= 0 && jy < A.npix) {
               const int pix = off + jy * A.npix + jx;
-              if (A.lam) dot[vi] += (R)A.lam[pix] * w * cw[k];
-              else atomicAdd(A.maps + pix, (double)(w * cw[k]));
+              if (A.lam) dot[vi] += A.lam[pix] * w * cw[k];
+              else atomicAdd(A.maps + pix, to_f64(w * cw[k]));
             }
           }
         }
@@ -225,8 +227,8 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
     };
     for (int base = 0; base < A.nrep; base += 32) {
       // replicas base..base+31 any particle of the warp may reach (warp-uniform ballot)
-      unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, (float)A.cell_len, (float)A.chi_lo2,
-                                    (float)A.chi_hi2, (float)A.tan_half, (float)A.margin);
+      unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, A.g.cull_cell_len, A.g.cull_lo2, A.g.cull_hi2,
+                                    A.g.cull_tan_half, A.g.cull_margin);
       if (!valid) live = 0u;
       while (live) {
         const int q = base + __ffs(live) - 1;
@@ -264,6 +266,14 @@ template <typename R>
 static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs<R>& A);
 
 template <typename R>
+static void var_mirrors(LensVar<R>& V) {
+  for (int s = 0; s < PM_MAX_ZS; ++s) V.chi_s_r[s] = (R)V.chi_s[s];
+  V.wpref_r = (R)V.wpref;
+  V.d1_next_r = (R)V.d1_next;
+  V.inv_gp_half_r = (R)V.inv_gp_half;
+}
+
+template <typename R>
 cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
   LensArgs<R> A;
   fill_lens_args<R>(c, sh, use_pgd, A);
@@ -278,7 +288,7 @@ cudaError_t launch_lens(pm_ctx* c, const LensShell& sh, int use_pgd) {
 }
 
 template <typename R>
-cudaError_t launch_lens_dot2(pm_ctx* c, const LensShell& sel, int use_pgd, const double* lam, const LensDotVar& a,
+cudaError_t launch_lens_dot2(pm_ctx* c, const LensShell& sel, int use_pgd, const R* lam, const LensDotVar& a,
                              const LensDotVar& b) {
   LensArgs<R> A;
   fill_lens_args<R>(c, sel, use_pgd, A);
@@ -293,6 +303,7 @@ cudaError_t launch_lens_dot2(pm_ctx* c, const LensShell& sel, int use_pgd, const
     V.d1_next = in[v]->d1_next;
     V.inv_gp_half = 1.0 / in[v]->gp_half;
     V.acc = in[v]->acc;
+    var_mirrors(V);
   }
   A.lam = lam;
   long long blocks = (c->np + 255) / 256;
@@ -339,6 +350,7 @@ static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs
   V.tab_inva = chi_table<R>(c, T_INVA);
   V.qtab = qtable<R>(c, Q_CENTRAL);
   V.acc = nullptr;
+  var_mirrors(V);
   A.var[1] = V;
   A.sub = c->cfg.sub_evolution;
   A.tab_hinv = 1.0 / c->chi_tab_h;
@@ -348,6 +360,8 @@ static void fill_lens_args(pm_ctx* c, const LensShell& sh, int use_pgd, LensArgs
   A.gathers = nullptr;
   A.nz_mask = c->nz_mask;
   A.lam = nullptr;
+  A.g = geom_mirrors<R>(A.cell_len, A.chi_lo2, A.chi_hi2, A.fov_half, A.inv_dtheta, A.tan_half, A.margin,
+                        A.tab_hinv);
   A.nrep = sh.nrep;
   for (int q = 0; q < sh.nrep; ++q) A.rep[q] = sh.rep[q];
 }
@@ -366,7 +380,7 @@ cudaError_t launch_kappa_finalize(pm_ctx* c, double* out) {
 
 template cudaError_t launch_lens<float>(pm_ctx*, const LensShell&, int);
 template cudaError_t launch_lens<double>(pm_ctx*, const LensShell&, int);
-template cudaError_t launch_lens_dot2<float>(pm_ctx*, const LensShell&, int, const double*, const LensDotVar&,
+template cudaError_t launch_lens_dot2<float>(pm_ctx*, const LensShell&, int, const float*, const LensDotVar&,
                                              const LensDotVar&);
 template cudaError_t launch_lens_dot2<double>(pm_ctx*, const LensShell&, int, const double*, const LensDotVar&,
                                               const LensDotVar&);

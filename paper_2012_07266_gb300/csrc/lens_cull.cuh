@@ -50,14 +50,15 @@ __device__ __forceinline__ WarpBox warp_box(bool valid, float p0, float p1, floa
 // shells); within 1e-6 (relative, in chi^2) of either boundary the test is
 // redone in FP64, so that both precisions select the same particles.  The
 // forward, reverse and tangent projections share this test.
+// lo2r, hi2r: the bounds rounded to R on the host (no FP64 conversion per test).
 template <typename R>
 __device__ __forceinline__ bool in_shell(R chi2, const int (&gi)[3], const R (&f)[3], double cell_len, double lo2,
-                                         double hi2) {
+                                         double hi2, R lo2r, R hi2r) {
   if constexpr (sizeof(R) == 8) {
     return chi2 > lo2 && chi2 <= hi2;
   } else {
     const float band = 1e-6f * chi2;
-    if (fabsf(chi2 - (float)lo2) > band && fabsf(chi2 - (float)hi2) > band) return chi2 > (float)lo2 && chi2 <= (float)hi2;
+    if (fabsf(chi2 - lo2r) > band && fabsf(chi2 - hi2r) > band) return chi2 > lo2r && chi2 <= hi2r;
     double c2 = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -67,6 +68,20 @@ __device__ __forceinline__ bool in_shell(R chi2, const int (&gi)[3], const R (&f
     return c2 > lo2 && c2 <= hi2;
   }
 }
+
+// The exact FP64 value of an FP32 number, assembled from its IEEE-754 fields
+// with integer operations (normal numbers: exponent rebiased by 1023 - 127,
+// mantissa moved to the top of the 52-bit field); zeros, subnormals, infinities
+// and NaNs take the conversion instruction.
+__device__ __forceinline__ double exact_f64(float x) {
+  const unsigned b = __float_as_uint(x);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e == 0u || e == 0xffu) return (double)x;
+  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ double to_f64(float x) { return exact_f64(x); }
+__device__ __forceinline__ double to_f64(double x) { return x; }
 
 // false only if no position in the box can pass the shell, z > 0 and field-of-view
 // tests of the per-particle code under replica rp

@@ -56,6 +56,27 @@ struct LensShell {
   Replica rep[kMaxReplicas];
 };
 
+// Path-precision (R) and FP32 copies of a projection's FP64 scalar parameters,
+// rounded once on the host: on this GPU FP64 instructions, conversions
+// included, run at a small fraction of the FP32 rate, so the kernels' hot loops
+// take these copies instead of converting the FP64 fields at each use.
+template <typename R>
+struct GeomMirrors {
+  R cell_len, lo2, hi2, fov_half, inv_dtheta, tan_half, margin, tab_hinv;
+  float cull_cell_len, cull_lo2, cull_hi2, cull_tan_half, cull_margin;
+};
+
+template <typename R>
+inline GeomMirrors<R> geom_mirrors(double cell_len, double lo2, double hi2, double fov_half, double inv_dtheta,
+                                   double tan_half, double margin, double tab_hinv) {
+  GeomMirrors<R> g;
+  g.cell_len = (R)cell_len; g.lo2 = (R)lo2; g.hi2 = (R)hi2; g.fov_half = (R)fov_half;
+  g.inv_dtheta = (R)inv_dtheta; g.tan_half = (R)tan_half; g.margin = (R)margin; g.tab_hinv = (R)tab_hinv;
+  g.cull_cell_len = (float)cell_len; g.cull_lo2 = (float)lo2; g.cull_hi2 = (float)hi2;
+  g.cull_tan_half = (float)tan_half; g.cull_margin = (float)margin;
+  return g;
+}
+
 // kernel classes for launch counting and optional event timing
 enum KernelKind {
   KK_KDK_PAINT = 0, KK_PAINT, KK_FFT_X_FWD, KK_FFT_Y_FWD, KK_FFT_Z_FWD, KK_FFT_Z_OP, KK_FFT_Y_INV,
@@ -109,6 +130,7 @@ struct Layout {
   size_t tan_x, tan_p, tan_tmp, tan_f, tan_s, tan_maps, tan_ic;
   size_t qtab, qtab_f;  // lensing efficiency tables of n(z) sources: FP64 and FP32 mirror
   size_t adj_noise, adj_ckpt, adj_seg, adj_fseg, adj_sseg, adj_lx, adj_lp, adj_v, adj_vs, adj_paint, adj_ic;
+  size_t adj_lam;  // FP32 path: dL/dkappa rounded to FP32 for the projection transposes
   size_t tab_dd1, tab_dinva, tab_d1p, tab_d1m, tab_invap, tab_invam, sqrtp_p, sqrtp_m, adj_acc;
   int nck, nic;             // checkpoints, IC adjoint fields
   size_t ftab;              // FP32 mirrors of the chi tables (TabId order)
