@@ -100,37 +100,44 @@ __global__ void k_paint_weights(AdjState<R> s, const R* __restrict__ v0, const R
   if (j < np) one(j);
 }
 
-// the three cotangent components into one interleaved float4 mesh.  Each block
-// takes one contiguous run of PAINT4_RUN (spatially sorted) particles; when the
-// CIC footprint of the run fits a shared-memory tile of at most PAINT4_TILE
-// cells, the run is accumulated in the tile (three component planes) with
-// shared-memory atomics and the tile's non-zero cells are added to the mesh with
-// one 16-byte reduction each; otherwise (sparse runs, runs across the periodic
-// boundary) each corner of each particle is one 16-byte reduction (x, y, z in
-// one vector).  The mesh reductions' L2 throughput bounds the untiled form.
-constexpr int PAINT4_THREADS = 256, PAINT4_PPT = 4, PAINT4_RUN = PAINT4_THREADS * PAINT4_PPT;
-constexpr int PAINT4_TILE = 4000;  // 3 x 4 B per cell: 48 KB of static shared memory
+// Cotangent paint into per-cell interleaved meshes: NW = 3 components (one
+// cotangent set: x, y, z, unused into the float4 mesh mA) or NW = 6 (two sets
+// at the same positions: v_x, v_y, v_z, w_x into mA, w_y, w_z into the float2
+// mesh mB).  Each block takes one contiguous run of PAINT_RUN (spatially
+// sorted) particles; when the CIC footprint of the run fits a shared-memory
+// tile of at most PAINT_TILE / NW cells, the run is accumulated in the tile
+// (one plane per component) with shared-memory atomics and each non-zero tile
+// cell is added to the meshes with one 16-byte (and one 8-byte) reduction;
+// otherwise (sparse runs, runs across the periodic boundary) each corner of each
+// particle is one such reduction.  The mesh reductions' L2 throughput bounds the
+// untiled form.
+constexpr int PAINT_THREADS = 256, PAINT_PPT = 4, PAINT_RUN = PAINT_THREADS * PAINT_PPT;
+constexpr int PAINT_TILE = 12000;  // component-cells: 48 KB of static shared memory
 
-__device__ __forceinline__ void red_v4(float* p, float a, float b, float d) {
-  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(d), "f"(0.f)
+__device__ __forceinline__ void red_v4(float* p, float a, float b, float d, float e) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(d), "f"(e)
                : "memory");
 }
+__device__ __forceinline__ void red_v2(float* p, float a, float b) {
+  asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
 
-__global__ void __launch_bounds__(PAINT4_THREADS) k_paint_weights4(AdjState<float> s, const float* __restrict__ v0,
-                                                                   const float* __restrict__ v1,
-                                                                   const float* __restrict__ v2,
-                                                                   float* __restrict__ m4, int M, long long np) {
-  __shared__ float tile[3][PAINT4_TILE];
+template <int NW>
+__global__ void __launch_bounds__(PAINT_THREADS) k_paint_il(AdjState<float> s, const float* __restrict__ v,
+                                                            const float* __restrict__ w, float* __restrict__ mA,
+                                                            float* __restrict__ mB, int M, long long np) {
+  constexpr int CAP = PAINT_TILE / NW;
+  __shared__ float tile[NW][CAP];
   __shared__ unsigned box[6];  // lo x, y, z; hi x, y, z
-  const long long jb = (long long)blockIdx.x * PAINT4_RUN;
+  const long long jb = (long long)blockIdx.x * PAINT_RUN;
   const int tid = threadIdx.x;
   if (tid < 3) box[tid] = 0xffffffffu;
   else if (tid < 6) box[tid] = 0u;
-  int cell[PAINT4_PPT][3];
+  int cell[PAINT_PPT][3];
   unsigned lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
 #pragma unroll
-  for (int q = 0; q < PAINT4_PPT; ++q) {
-    const long long j = jb + q * PAINT4_THREADS + tid;
+  for (int q = 0; q < PAINT_PPT; ++q) {
+    const long long j = jb + q * PAINT_THREADS + tid;
     if (j < np) {
       unpack3(s.cell[j], cell[q]);
 #pragma unroll
@@ -154,22 +161,29 @@ __global__ void __launch_bounds__(PAINT4_THREADS) k_paint_weights4(AdjState<floa
     }
   }
   __syncthreads();
-  const long long nrun = np - jb < PAINT4_RUN ? np - jb : PAINT4_RUN;
   // tile extents: the run's cells plus the +1 CIC corner along each axis
   const int ex = (int)(box[3] - box[0]) + 2, ey = (int)(box[4] - box[1]) + 2, ez = (int)(box[5] - box[2]) + 2;
   const long long vol = (long long)ex * ey * ez;
-  const bool tiled = vol <= PAINT4_TILE;
+  const bool tiled = vol <= CAP;
   if (tiled) {
-    for (int t = tid; t < vol; t += PAINT4_THREADS) tile[0][t] = tile[1][t] = tile[2][t] = 0.f;
+    for (int t = tid; t < vol; t += PAINT_THREADS)
+#pragma unroll
+      for (int c = 0; c < NW; ++c) tile[c][t] = 0.f;
     __syncthreads();
   }
 #pragma unroll
-  for (int q = 0; q < PAINT4_PPT; ++q) {
-    const long long j = jb + q * PAINT4_THREADS + tid;
+  for (int q = 0; q < PAINT_PPT; ++q) {
+    const long long j = jb + q * PAINT_THREADS + tid;
     if (j >= np) continue;
     const float fx = s.fx[j], fy = s.fy[j], fz = s.fz[j];
     const float gx = 1.f - fx, gy = 1.f - fy, gz = 1.f - fz;
-    const float a = v0[j], b = v1[j], d = v2[j];
+    float u[NW];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) u[c] = v[j + c * np];
+    if constexpr (NW == 6) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) u[3 + c] = w[j + c * np];
+    }
     const float wr[4] = {gz * gy, gz * fy, fz * gy, fz * fy};
     if (tiled) {
       const int tx = cell[q][0] - (int)box[0], ty = cell[q][1] - (int)box[1], tz = cell[q][2] - (int)box[2];
@@ -178,21 +192,26 @@ __global__ void __launch_bounds__(PAINT4_THREADS) k_paint_weights4(AdjState<floa
         const int row = ((tz + (r >> 1)) * ey + ty + (r & 1)) * ex + tx;
 #pragma unroll
         for (int dx = 0; dx < 2; ++dx) {
-          const float w = wr[r] * (dx ? fx : gx);
-          atomicAdd(&tile[0][row + dx], w * a);
-          atomicAdd(&tile[1][row + dx], w * b);
-          atomicAdd(&tile[2][row + dx], w * d);
+          const float wt = wr[r] * (dx ? fx : gx);
+#pragma unroll
+          for (int c = 0; c < NW; ++c) atomicAdd(&tile[c][row + dx], wt * u[c]);
         }
       }
     } else {
-      const Corners c = corners(M, cell[q][0], cell[q][1], cell[q][2]);
-      const unsigned rows[4] = {c.r00, c.r01, c.r10, c.r11};
+      const Corners cc = corners(M, cell[q][0], cell[q][1], cell[q][2]);
+      const unsigned rows[4] = {cc.r00, cc.r01, cc.r10, cc.r11};
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
 #pragma unroll
         for (int dx = 0; dx < 2; ++dx) {
-          const float w = wr[r] * (dx ? fx : gx);
-          red_v4(m4 + 4ull * (rows[r] + (dx ? c.x1 : c.x0)), w * a, w * b, w * d);
+          const float wt = wr[r] * (dx ? fx : gx);
+          const unsigned o = rows[r] + (dx ? cc.x1 : cc.x0);
+          if constexpr (NW == 6) {
+            red_v4(mA + 4ull * o, wt * u[0], wt * u[1], wt * u[2], wt * u[3]);
+            red_v2(mB + 2ull * o, wt * u[4], wt * u[5]);
+          } else {
+            red_v4(mA + 4ull * o, wt * u[0], wt * u[1], wt * u[2], 0.f);
+          }
         }
       }
     }
@@ -201,15 +220,27 @@ __global__ void __launch_bounds__(PAINT4_THREADS) k_paint_weights4(AdjState<floa
   __syncthreads();
   // flush: tile cell (x, y, z) is mesh cell box_lo + (x, y, z), periodic (the +1 corner of the
   // last cell of an axis is cell 0)
-  for (int t = tid; t < vol; t += PAINT4_THREADS) {
-    const float u0 = tile[0][t], u1 = tile[1][t], u2 = tile[2][t];
-    if (u0 == 0.f && u1 == 0.f && u2 == 0.f) continue;
+  for (int t = tid; t < vol; t += PAINT_THREADS) {
+    float u[NW];
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+      u[c] = tile[c][t];
+      any |= u[c] != 0.f;
+    }
+    if (!any) continue;
     const int x = t % ex, yz = t / ex, y = yz % ey, z = yz / ey;
     int gx = (int)box[0] + x, gy = (int)box[1] + y, gz = (int)box[2] + z;
     gx -= gx >= M ? M : 0;
     gy -= gy >= M ? M : 0;
     gz -= gz >= M ? M : 0;
-    red_v4(m4 + 4ull * (((unsigned)gz * M + gy) * (unsigned)M + gx), u0, u1, u2);
+    const unsigned o = ((unsigned)gz * M + gy) * (unsigned)M + gx;
+    if constexpr (NW == 6) {
+      red_v4(mA + 4ull * o, u[0], u[1], u[2], u[3]);
+      red_v2(mB + 2ull * o, u[4], u[5]);
+    } else {
+      red_v4(mA + 4ull * o, u[0], u[1], u[2], 0.f);
+    }
   }
 }
 
@@ -562,8 +593,15 @@ void adj_paint_weights(const AdjState<R>& s, const R* v, R* const* meshes, int M
 void adj_paint_weights4(const AdjState<float>& s, const float* v, float* mesh4, int M, long long np, cudaStream_t st,
                         Prof* pf) {
   ProfScope ps(pf, KK_ADJ_PAINT, st, np * (4.0 + 6.0 * sizeof(float)) + 4.0 * (double)M * M * M * sizeof(float));
-  const long long nb = (np + PAINT4_RUN - 1) / PAINT4_RUN;
-  if (nb > 0) k_paint_weights4<<<(unsigned)nb, PAINT4_THREADS, 0, st>>>(s, v, v + np, v + 2 * np, mesh4, M, np);
+  const long long nb = (np + PAINT_RUN - 1) / PAINT_RUN;
+  if (nb > 0) k_paint_il<3><<<(unsigned)nb, PAINT_THREADS, 0, st>>>(s, v, nullptr, mesh4, nullptr, M, np);
+}
+
+void adj_paint_weights6(const AdjState<float>& s, const float* v, const float* w, float* mesh4, float* mesh2, int M,
+                        long long np, cudaStream_t st, Prof* pf) {
+  ProfScope ps(pf, KK_ADJ_PAINT, st, np * (4.0 + 9.0 * sizeof(float)) + 6.0 * (double)M * M * M * sizeof(float));
+  const long long nb = (np + PAINT_RUN - 1) / PAINT_RUN;
+  if (nb > 0) k_paint_il<6><<<(unsigned)nb, PAINT_THREADS, 0, st>>>(s, v, w, mesh4, mesh2, M, np);
 }
 
 template <typename R>

@@ -53,16 +53,21 @@ template <typename R>
 cudaError_t spectral_forward_xy(R* const* real_in, int nin, void* const* ubufs, int n, int P, const SpecParams& sp,
                                 cudaStream_t s, Prof* prof);
 
-// the same for three FP32 meshes interleaved per cell as float4 (FP32 only; the FP64
-// path returns cudaErrorInvalidValue)
+// the same for the first nl values of each cell of an FP32 mesh interleaved per cell
+// with `lanes` values (lanes 4: nl 3 or 4; lanes 2: nl 2), into ubufs[0 .. nl-1] (FP32
+// only; other combinations and the FP64 path return cudaErrorInvalidValue)
 template <typename R>
-cudaError_t spectral_forward_xy_il4(const R* il, void* const* ubufs, int n, int P, const SpecParams& sp,
-                                    cudaStream_t s, Prof* prof);
+cudaError_t spectral_forward_xy_il(const R* il, int lanes, int nl, void* const* ubufs, int n, int P,
+                                   const SpecParams& sp, cudaStream_t s, Prof* prof);
 
 // paint three cotangent components v (3 x np) into one FP32 mesh interleaved per cell as
 // float4 (x, y, z, unused): one 16-byte vector reduction per corner
 void adj_paint_weights4(const AdjState<float>& s, const float* v, float* mesh4, int M, long long np, cudaStream_t st,
                         Prof* pf);
+// paint two cotangent sets at the same positions, v and w (3 x np each): v_x, v_y, v_z, w_x
+// into the float4-interleaved mesh4, w_y, w_z into the float2-interleaved mesh2
+void adj_paint_weights6(const AdjState<float>& s, const float* v, const float* w, float* mesh4, float* mesh2, int M,
+                        long long np, cudaStream_t st, Prof* pf);
 
 template <typename R>
 void adj_paint_weights(const AdjState<R>& s, const R* v, R* const* meshes, int M, long long np, cudaStream_t st,

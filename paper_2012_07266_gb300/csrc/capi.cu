@@ -707,7 +707,7 @@ cudaError_t mesh_vjp(pm_ctx* c, const AdjState<R>& st, const R* v, bool pgd_part
     // FP32: the three cotangent components in one float4-interleaved mesh
     if ((e = cudaMemsetAsync(pm[0], 0, 4 * c->mesh_elems * sizeof(float), s))) return e;
     adj_paint_weights4(st, v, pm[0], c->M, c->np, s, &c->prof);
-    if ((e = spectral_forward_xy_il4<R>(pm[0], ub, c->M, c->P, sp, s, &c->prof))) return e;
+    if ((e = spectral_forward_xy_il<R>(pm[0], 4, 3, ub, c->M, c->P, sp, s, &c->prof))) return e;
     if ((e = spectral_transpose_pre<R>(pm, 3, 3, pgd_part ? 3 : 0, ub, c->ws + c->L.cbuf, phi, c->M, c->P, sp, s,
                                        &c->prof)))
       return e;
@@ -741,12 +741,16 @@ cudaError_t mesh_vjp_pair(pm_ctx* c, const AdjState<R>& st, const R* vF, R* cons
   cudaError_t e;
   R* phi = rp<R>(c, c->L.rho);
   if constexpr (std::is_same<R, float>::value) {
-    // FP32: each set painted into one float4-interleaved mesh
-    for (int g = 0; g < 2; ++g) {
-      if ((e = cudaMemsetAsync(pm[0], 0, 4 * c->mesh_elems * sizeof(float), s))) return e;
-      adj_paint_weights4(st, g ? vS : vF, pm[0], c->M, c->np, s, &c->prof);
-      if ((e = spectral_forward_xy_il4<R>(pm[0], ub + 3 * g, c->M, c->P, sp, s, &c->prof))) return e;
-    }
+    // FP32: both sets painted in one pass, vF_x, vF_y, vF_z, vS_x interleaved per cell as
+    // float4 in the cotangent scratch and vS_y, vS_z as float2 in the density and spectrum
+    // scratch (free until the transposed z pass writes its spectrum there; 2 x 4 M^3 bytes
+    // fit, the spectrum alone being larger than one real mesh)
+    float* m2 = rp<float>(c, c->L.rho);
+    if ((e = cudaMemsetAsync(pm[0], 0, 4 * c->mesh_elems * sizeof(float), s))) return e;
+    if ((e = cudaMemsetAsync(m2, 0, 2 * c->mesh_elems * sizeof(float), s))) return e;
+    adj_paint_weights6(st, vF, vS, pm[0], m2, c->M, c->np, s, &c->prof);
+    if ((e = spectral_forward_xy_il<R>(pm[0], 4, 4, ub, c->M, c->P, sp, s, &c->prof))) return e;
+    if ((e = spectral_forward_xy_il<R>(m2, 2, 2, ub + 4, c->M, c->P, sp, s, &c->prof))) return e;
     R* ins[6] = {};
     if ((e = spectral_transpose_pre<R>(ins, 6, 6, 0, ub, c->ws + c->L.cbuf, phi, c->M, c->P, sp, s, &c->prof)))
       return e;

@@ -80,8 +80,14 @@ struct Launch {
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TT::SMEM);
     cudaFuncSetAttribute(k_fft_cols_tma<R, N, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          TT::SMEM_DUAL);
-    if constexpr (std::is_same<R, float>::value)
-      cudaFuncSetAttribute(k_fft_x_r2c_il4<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, RowTile3<N>::SMEM);
+    if constexpr (std::is_same<R, float>::value) {
+      cudaFuncSetAttribute(k_fft_x_r2c_il<N, 4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           RowTileIL<N, 3>::SMEM);
+      cudaFuncSetAttribute(k_fft_x_r2c_il<N, 4, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           RowTileIL<N, 4>::SMEM);
+      cudaFuncSetAttribute(k_fft_x_r2c_il<N, 2, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           RowTileIL<N, 2>::SMEM);
+    }
     // an attribute this device refuses would otherwise surface as the error of an unrelated
     // later launch check; a kernel that really needs it fails at its own launch
     cudaGetLastError();
@@ -187,19 +193,23 @@ struct Launch {
     return e ? e : cudaGetLastError();
   }
 
-  // x and y forward passes of three FP32 meshes interleaved per cell as float4
-  static cudaError_t forward_xy_il4(const R* il, void* const* ubufs, int P, const SpecParams& sp, cudaStream_t s,
-                                    Prof* pf) {
+  // x pass of NL lanes of an FP32 mesh interleaved per cell (LANES values per cell) into
+  // ubufs[0 .. NL-1], then the y pass of each
+  template <int LANES, int NL>
+  static cudaError_t forward_xy_il(const R* il, void* const* ubufs, int P, const SpecParams& sp, cudaStream_t s,
+                                   Prof* pf) {
     if constexpr (std::is_same<R, float>::value) {
       attrs();
       {
-        ProfScope ps(pf, KK_ADJ_FFT, s, 4.0 * RB + 3.0 * CB);  // the float4 mesh read, three half spectra written
-        k_fft_x_r2c_il4<N><<<(long long)N * N / RowTile3<N>::ROWS, RowTile3<N>::THREADS, RowTile3<N>::SMEM, s>>>(
-            reinterpret_cast<const float4*>(il), reinterpret_cast<float2*>(ubufs[0]),
-            reinterpret_cast<float2*>(ubufs[1]), reinterpret_cast<float2*>(ubufs[2]), P);
+        // the interleaved mesh read, NL half spectra written
+        ProfScope ps(pf, KK_ADJ_FFT, s, (double)LANES * RB + (double)NL * CB);
+        ILOut o = {};
+        for (int q = 0; q < NL; ++q) o.p[q] = reinterpret_cast<float2*>(ubufs[q]);
+        k_fft_x_r2c_il<N, LANES, NL><<<(long long)N * N / RowTileIL<N, NL>::ROWS, RowTileIL<N, NL>::THREADS,
+                                       RowTileIL<N, NL>::SMEM, s>>>(il, o, P);
       }
       cudaError_t e = cudaSuccess;
-      for (int i = 0; i < 3 && !e; ++i) e = y(reinterpret_cast<C*>(ubufs[i]), P, false, s, pf, KK_ADJ_FFT, sp.err);
+      for (int i = 0; i < NL && !e; ++i) e = y(reinterpret_cast<C*>(ubufs[i]), P, false, s, pf, KK_ADJ_FFT, sp.err);
       return e ? e : cudaGetLastError();
     } else {
       return cudaErrorInvalidValue;
@@ -319,9 +329,12 @@ cudaError_t spectral_forward_xy(R* const* real_in, int nin, void* const* ubufs, 
 }
 
 template <typename R>
-cudaError_t spectral_forward_xy_il4(const R* il, void* const* ubufs, int n, int P, const SpecParams& sp,
-                                    cudaStream_t s, Prof* pf) {
-  PM_FFT_DISPATCH(n, L::forward_xy_il4(il, ubufs, P, sp, s, pf));
+cudaError_t spectral_forward_xy_il(const R* il, int lanes, int nl, void* const* ubufs, int n, int P,
+                                   const SpecParams& sp, cudaStream_t s, Prof* pf) {
+  if (lanes == 4 && nl == 3) { PM_FFT_DISPATCH(n, (L::template forward_xy_il<4, 3>(il, ubufs, P, sp, s, pf))); }
+  if (lanes == 4 && nl == 4) { PM_FFT_DISPATCH(n, (L::template forward_xy_il<4, 4>(il, ubufs, P, sp, s, pf))); }
+  if (lanes == 2 && nl == 2) { PM_FFT_DISPATCH(n, (L::template forward_xy_il<2, 2>(il, ubufs, P, sp, s, pf))); }
+  return cudaErrorInvalidValue;
 }
 
 template cudaError_t spectral_transpose<PM_REAL>(PM_REAL* const*, int, int, void* const*, void*, PM_REAL*, int, int,
@@ -330,8 +343,8 @@ template cudaError_t spectral_transpose_pre<PM_REAL>(PM_REAL* const*, int, int, 
                                                       int, int, const SpecParams&, cudaStream_t, Prof*);
 template cudaError_t spectral_forward_xy<PM_REAL>(PM_REAL* const*, int, void* const*, int, int, const SpecParams&,
                                                    cudaStream_t, Prof*);
-template cudaError_t spectral_forward_xy_il4<PM_REAL>(const PM_REAL*, void* const*, int, int, const SpecParams&,
-                                                       cudaStream_t, Prof*);
+template cudaError_t spectral_forward_xy_il<PM_REAL>(const PM_REAL*, int, int, void* const*, int, int,
+                                                      const SpecParams&, cudaStream_t, Prof*);
 template cudaError_t fft3d_r2c<PM_REAL>(const PM_REAL*, void*, int, int, cudaStream_t, Prof*, int*);
 template cudaError_t spectral_apply<PM_REAL>(const PM_REAL*, void*, void* const*, PM_REAL* const*, int, int, int,
                                               const SpecParams&, cudaStream_t, Prof*, int);

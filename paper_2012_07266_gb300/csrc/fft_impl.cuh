@@ -538,27 +538,41 @@ k_fft_x_r2c(const R* __restrict__ in, typename CT<R>::T* __restrict__ out, int P
   for (int hh = threadIdx.x; hh < ROWS; hh += blockDim.x) untangle(hh, H);
 }
 
-// x pass, forward, of three FP32 meshes stored interleaved per cell as float4 (x, y, z
-// and an unused fourth value; the adjoint's cotangent meshes, painted with one vector
-// reduction per corner): rows of N cells -> three half-spectrum rows.  The three
-// component rows of a block share the shared-memory stages of one x r2c.
-// A quarter of the x pass's rows per block (4 row triples at N = 512: 30 KB of shared
-// memory, 64 threads): more resident blocks hide the float4 loads (measured 4 ms per pm256
-// reverse sweep faster than 16 or 8 row triples).
-template <int N> struct RowTile3 {
+// x pass, forward, of FP32 meshes stored interleaved per cell (the adjoint's cotangent
+// meshes, painted with one vector reduction per corner): rows of N cells -> one
+// half-spectrum row per component.  The component rows of a block share the
+// shared-memory stages of one x r2c.  A quarter of the x pass's rows per block (4 row
+// triples at N = 512: 30 KB of shared memory, 64 threads): more resident blocks hide the
+// vector loads (measured 4 ms per pm256 reverse sweep faster than 16 or 8 row triples).
+template <int N, int NL> struct RowTileIL {
   static constexpr int H = N / 2, T = RowTile<float, N>::T, LD = PadLen<H>::value + 1;
   static constexpr int ROWS = RowTile<float, N>::ROWS / 4 > 0 ? RowTile<float, N>::ROWS / 4 : 1;
   static constexpr int THREADS = ROWS * T;
-  static constexpr int SMEM = (H + H + 2 + 3 * ROWS * LD) * 8;
+  static constexpr int SMEM = (H + H + 2 + NL * ROWS * LD) * 8;
 };
 
-template <int N>
-__global__ void __launch_bounds__(RowTile3<N>::THREADS)
-k_fft_x_r2c_il4(const float4* __restrict__ in, float2* __restrict__ out0, float2* __restrict__ out1,
-                float2* __restrict__ out2, int P) {
+struct ILOut { float2* p[4]; };
+
+template <int LANES> struct LaneVec;
+template <> struct LaneVec<4> {
+  using T = float4;
+  __device__ static float get(const float4& v, int c) { return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w; }
+};
+template <> struct LaneVec<2> {
+  using T = float2;
+  __device__ static float get(const float2& v, int c) { return c == 0 ? v.x : v.y; }
+};
+
+// x pass of a mesh interleaved per cell (LANES = 4: float4, LANES = 2: float2):
+// the first NL lanes of each row are transformed as NL real rows into NL half
+// spectra (out.p[0 .. NL-1]).
+template <int N, int LANES, int NL>
+__global__ void __launch_bounds__(RowTileIL<N, NL>::THREADS)
+k_fft_x_r2c_il(const float* __restrict__ in_f, ILOut out, int P) {
   using C = float2;
-  constexpr int H = N / 2, ROWS = RowTile3<N>::ROWS, T = RowTile3<N>::T, LD = RowTile3<N>::LD;
-  constexpr int THR = RowTile3<N>::THREADS;
+  using VT = typename LaneVec<LANES>::T;
+  constexpr int H = N / 2, ROWS = RowTileIL<N, NL>::ROWS, T = RowTileIL<N, NL>::T, LD = RowTileIL<N, NL>::LD;
+  constexpr int THR = RowTileIL<N, NL>::THREADS;
   extern __shared__ unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* tu = tw + H;
@@ -568,12 +582,12 @@ k_fft_x_r2c_il4(const float4* __restrict__ in, float2* __restrict__ out0, float2
   const long long row0 = (long long)blockIdx.x * ROWS;
   {
     // cells 2m and 2m + 1 of a row make complex element m of each component's half-length row
-    const float4* inr = in + row0 * N;
+    const VT* inr = reinterpret_cast<const VT*>(in_f) + row0 * N;
     constexpr int PER = ROWS * H / THR, B = PER < 4 ? PER : 4;
     static_assert(PER % B == 0, "load batches");
 #pragma unroll 1
     for (int q0 = 0; q0 < PER; q0 += B) {
-      float4 a[B], b[B];
+      VT a[B], b[B];
 #pragma unroll
       for (int q = 0; q < B; ++q) {
         const int e = threadIdx.x + (q0 + q) * THR;
@@ -585,21 +599,20 @@ k_fft_x_r2c_il4(const float4* __restrict__ in, float2* __restrict__ out0, float2
         const int e = threadIdx.x + (q0 + q) * THR;
         const int hh = e / H, m = e - hh * H;
         const int o = hh * LD + pad16(m);
-        buf[o] = C{a[q].x, b[q].x};
-        buf[ROWS * LD + o] = C{a[q].y, b[q].y};
-        buf[2 * ROWS * LD + o] = C{a[q].z, b[q].z};
+#pragma unroll
+        for (int c = 0; c < NL; ++c) buf[c * ROWS * LD + o] = C{LaneVec<LANES>::get(a[q], c), LaneVec<LANES>::get(b[q], c)};
       }
     }
   }
   __syncthreads();
   const int h = threadIdx.x / T, t = threadIdx.x - h * T;
 #pragma unroll 1
-  for (int q = 0; q < 3; ++q) fft_column<C, H, false, 1, LD, 1, typename RowTile<float, N>::PL>(buf + q * ROWS * LD, h, t, tw);
+  for (int q = 0; q < NL; ++q) fft_column<C, H, false, 1, LD, 1, typename RowTile<float, N>::PL>(buf + q * ROWS * LD, h, t, tw);
   // X[k] = (Z[k] + conj Z[H-k]) / 2 + e^{-2 pi i k / N} (Z[k] - conj Z[H-k]) / (2i), k <= H
 #pragma unroll 1
-  for (int q = 0; q < 3; ++q) {
+  for (int q = 0; q < NL; ++q) {
     const C* bq = buf + q * ROWS * LD;
-    float2* outb = (q == 0 ? out0 : q == 1 ? out1 : out2) + row0 * P;
+    float2* outb = out.p[q] + row0 * P;
     auto untangle = [&](int hh, int k) {
       const C zk = bq[hh * LD + pad16(k % H)];
       const C zm = cconj(bq[hh * LD + pad16((H - k) % H)]);
