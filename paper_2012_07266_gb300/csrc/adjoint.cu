@@ -248,9 +248,13 @@ __global__ void __launch_bounds__(PAINT_THREADS) k_paint_il(AdjState<float> s, c
 // dot = sum_j lamp_j . readout(mesh)(x_j).  TWO: a second transpose at the same
 // positions in the same pass, + sum_c w_c grad readout(mesh2_c) (the PGD
 // transpose of a lightcone step fused with the kick transpose of the next step).
-// Each block walks one contiguous run of the (spatially sorted) particles, so
-// that its gathers reuse mesh rows in L2 (-6% against a grid-stride loop); each
-// particle's dot term is formed in the path precision and accumulated in FP64.
+// Each block takes one contiguous run of READ_RUN (spatially sorted) particles;
+// when the run's CIC footprint fits a shared-memory tile of READ_TILE bytes for
+// all the meshes read, the block first copies that box of every mesh into the
+// tile (row segments, coalesced along x) and the particles gather from shared
+// memory; otherwise (sparse runs, runs across the periodic boundary) they gather
+// from global memory.  Each particle's dot term is formed in the path precision
+// and accumulated in FP64.
 template <typename R>
 struct ReadoutMeshes {
   const R* m[3];   // meshes read and differentiated with cotangent v
@@ -259,20 +263,91 @@ struct ReadoutMeshes {
   const R* w[3];
 };
 
+constexpr int READ_THREADS = 256, READ_PPT = 4, READ_RUN = READ_THREADS * READ_PPT;
+constexpr int READ_TILE = 48000;  // bytes of static shared memory
+
 template <typename R, bool TWO>
-__global__ void k_readout_grad(AdjState<R> s, ReadoutMeshes<R> rm, const R* __restrict__ phi, R mass,
-                               R* __restrict__ lx, const R* __restrict__ lp, double* dot, int M, long long np) {
+__global__ void __launch_bounds__(READ_THREADS) k_readout_grad(AdjState<R> s, ReadoutMeshes<R> rm,
+                                                               const R* __restrict__ phi, R mass,
+                                                               R* __restrict__ lx, const R* __restrict__ lp,
+                                                               double* dot, int M, long long np) {
+  constexpr int NM = TWO ? 7 : 4;  // meshes read: m[0..2], phi, m2[0..2]
+  constexpr int CAP = READ_TILE / (NM * (int)sizeof(R));
+  __shared__ R tile[NM][CAP];
+  __shared__ unsigned box[6];  // lo x, y, z; hi x, y, z
+  const long long jb = (long long)blockIdx.x * READ_RUN;
+  const int tid = threadIdx.x;
+  if (tid < 3) box[tid] = 0xffffffffu;
+  else if (tid < 6) box[tid] = 0u;
+  unsigned lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
+#pragma unroll
+  for (int q = 0; q < READ_PPT; ++q) {
+    const long long j = jb + q * READ_THREADS + tid;
+    if (j < np) {
+      int ci[3];
+      unpack3(s.cell[j], ci);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = min(lo[a], (unsigned)ci[a]);
+        hi[a] = max(hi[a], (unsigned)ci[a]);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = __reduce_min_sync(0xffffffffu, lo[a]);
+    hi[a] = __reduce_max_sync(0xffffffffu, hi[a]);
+  }
+  if ((tid & 31) == 0) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      atomicMin(&box[a], lo[a]);
+      atomicMax(&box[3 + a], hi[a]);
+    }
+  }
+  __syncthreads();
+  const int ex = (int)(box[3] - box[0]) + 2, ey = (int)(box[4] - box[1]) + 2, ez = (int)(box[5] - box[2]) + 2;
+  const long long vol = (long long)ex * ey * ez;
+  const bool tiled = vol <= CAP;
+  // mesh mi (compile-time after unrolling): m[0..2], phi, m2[0..2]
+  auto src = [&](int mi) -> const R* {
+    return mi < 3 ? rm.m[mi] : mi == 3 ? phi : rm.m2[mi - 4];
+  };
+  if (tiled) {
+    // tile cell (x, y, z) holds mesh cell box_lo + (x, y, z), periodic
+    for (int t = tid; t < vol; t += READ_THREADS) {
+      const int x = t % ex, yz = t / ex, y = yz % ey, z = yz / ey;
+      int gx = (int)box[0] + x, gy = (int)box[1] + y, gz = (int)box[2] + z;
+      gx -= gx >= M ? M : 0;
+      gy -= gy >= M ? M : 0;
+      gz -= gz >= M ? M : 0;
+      const unsigned o = ((unsigned)gz * M + gy) * (unsigned)M + gx;
+#pragma unroll
+      for (int mi = 0; mi < NM; ++mi) tile[mi][t] = src(mi)[o];
+    }
+    __syncthreads();
+  }
   double dsum = 0.0;
-  const long long per = (np + gridDim.x - 1) / gridDim.x;
-  const long long jb = blockIdx.x * per, je = jb + per < np ? jb + per : np;
-  for (long long j = jb + threadIdx.x; j < je; j += blockDim.x) {
-    int i[3];
-    unpack3(s.cell[j], i);
+#pragma unroll 1
+  for (int q = 0; q < READ_PPT; ++q) {
+    const long long j = jb + q * READ_THREADS + tid;
+    if (j >= np) continue;
+    int ci[3];
+    unpack3(s.cell[j], ci);  // read again: a runtime-indexed per-thread array would sit in local memory
     const R f[3] = {s.fx[j], s.fy[j], s.fz[j]};
-    const Corners cc = corners(M, i[0], i[1], i[2]);
-    // corner k = (dx, dy, dz) = (k & 1, k >> 1 & 1, k >> 2), 32-bit offsets
-    const unsigned o[8] = {cc.r00 + cc.x0, cc.r00 + cc.x1, cc.r01 + cc.x0, cc.r01 + cc.x1,
-                           cc.r10 + cc.x0, cc.r10 + cc.x1, cc.r11 + cc.x0, cc.r11 + cc.x1};
+    // corner k = (dx, dy, dz) = (k & 1, k >> 1 & 1, k >> 2): its offset in the tile or the mesh
+    unsigned o[8];
+    if (tiled) {
+      const int tx = ci[0] - (int)box[0], ty = ci[1] - (int)box[1], tz = ci[2] - (int)box[2];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[k] = ((tz + (k >> 2)) * ey + ty + ((k >> 1) & 1)) * ex + tx + (k & 1);
+    } else {
+      const Corners cc = corners(M, ci[0], ci[1], ci[2]);
+      o[0] = cc.r00 + cc.x0; o[1] = cc.r00 + cc.x1; o[2] = cc.r01 + cc.x0; o[3] = cc.r01 + cc.x1;
+      o[4] = cc.r10 + cc.x0; o[5] = cc.r10 + cc.x1; o[6] = cc.r11 + cc.x0; o[7] = cc.r11 + cc.x1;
+    }
+    auto at = [&](int mi, int k) -> R { return tiled ? tile[mi][o[k]] : src(mi)[o[k]]; };
     const R v[3] = {rm.v[0][j], rm.v[1][j], rm.v[2][j]};
     R w[3] = {R(0), R(0), R(0)};
     if constexpr (TWO) {
@@ -286,17 +361,17 @@ __global__ void k_readout_grad(AdjState<R> s, ReadoutMeshes<R> rm, const R* __re
       const int dx = k & 1, dy = (k >> 1) & 1, dz = k >> 2;
       const R wx = dx ? f[0] : R(1) - f[0], wy = dy ? f[1] : R(1) - f[1], wz = dz ? f[2] : R(1) - f[2];
       const R sx = dx ? R(1) : R(-1), sy = dy ? R(1) : R(-1), sz = dz ? R(1) : R(-1);
-      R q = mass * phi[o[k]];
+      R qv = mass * at(3, k);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const R mv = rm.m[c][o[k]];
-        q += v[c] * mv;
+        const R mv = at(c, k);
+        qv += v[c] * mv;
         val[c] += wx * wy * wz * mv;
-        if constexpr (TWO) q += w[c] * rm.m2[c][o[k]];
+        if constexpr (TWO) qv += w[c] * at(4 + c, k);
       }
-      g[0] += sx * wy * wz * q;
-      g[1] += wx * sy * wz * q;
-      g[2] += wx * wy * sz * q;
+      g[0] += sx * wy * wz * qv;
+      g[1] += wx * sy * wz * qv;
+      g[2] += wx * wy * sz * qv;
     }
     lx[j] += g[0];
     lx[j + np] += g[1];
@@ -613,7 +688,8 @@ void adj_readout_grad(const AdjState<R>& s, R* const* meshes, const R* v, const 
     rm.m[c] = meshes[c];
     rm.v[c] = v + c * np;
   }
-  k_readout_grad<R, false><<<blocks_for(np), 256, 0, st>>>(s, rm, phi, (R)mass, lx, lp, dot, M, np);
+  const long long nb = (np + READ_RUN - 1) / READ_RUN;
+  if (nb > 0) k_readout_grad<R, false><<<(unsigned)nb, READ_THREADS, 0, st>>>(s, rm, phi, (R)mass, lx, lp, dot, M, np);
 }
 
 template <typename R>
@@ -628,7 +704,8 @@ void adj_readout_grad2(const AdjState<R>& s, R* const* meshes, const R* v, R* co
     rm.m2[c] = meshes2[c];
     rm.w[c] = w + c * np;
   }
-  k_readout_grad<R, true><<<blocks_for(np), 256, 0, st>>>(s, rm, phi, (R)mass, lx, lp, dot, M, np);
+  const long long nb = (np + READ_RUN - 1) / READ_RUN;
+  if (nb > 0) k_readout_grad<R, true><<<(unsigned)nb, READ_THREADS, 0, st>>>(s, rm, phi, (R)mass, lx, lp, dot, M, np);
 }
 
 template <typename R>
