@@ -111,7 +111,7 @@ __global__ void k_paint_weights(AdjState<R> s, const R* __restrict__ v0, const R
 // otherwise (sparse runs, runs across the periodic boundary) each corner of each
 // particle is one such reduction.  The mesh reductions' L2 throughput bounds the
 // untiled form.
-constexpr int PAINT_THREADS = 256, PAINT_PPT = 4, PAINT_RUN = PAINT_THREADS * PAINT_PPT;
+constexpr int PAINT_THREADS = 256, PAINT_PPT = 2, PAINT_RUN = PAINT_THREADS * PAINT_PPT;
 constexpr int PAINT_TILE = 12000;  // component-cells: 48 KB of static shared memory
 
 __device__ __forceinline__ void red_v4(float* p, float a, float b, float d, float e) {

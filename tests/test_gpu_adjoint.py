@@ -47,6 +47,12 @@ CASES = [
     (1, dict(lpt_order=2, pgd=1, zs=(0.8, 1.0), ckpt_every=6), 1e-6, 1e-6),
     (0, dict(lpt_order=2, pgd=1, zs=(0.8, 1.0), ckpt_every=100), 2e-3, 5e-3),
     (0, dict(ckpt_every=6), 2e-3, 5e-3),
+    # as many particles as mesh cells: runs of sorted particles then cover ~1000-2000 cells, so
+    # both forms of the cotangent paint and of the readout gradient run in the same sweep (the
+    # shared-memory tile for the runs whose box fits it -- about half of the readout gradient's
+    # runs of 1024 particles, 10-15% of the paired ones -- and per-corner global reductions and
+    # gathers for the others)
+    (0, dict(nc=32, nmesh=32, lpt_order=2, pgd=1, zs=(0.8, 1.0), ckpt_every=2), 2e-3, 5e-3),
 ]
 
 
