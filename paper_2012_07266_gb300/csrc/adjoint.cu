@@ -493,6 +493,22 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
     R gx[3] = {0, 0, 0}, gp[3] = {0, 0, 0}, gs[3] = {0, 0, 0};
     const WarpBox box =
         warp_box(valid, (float)ci[0] + (float)cf[0], (float)ci[1] + (float)cf[1], (float)ci[2] + (float)cf[2]);
+    // the particle's PGD displacement (cells), CIC-gathered from the three PGD meshes
+    auto gather_s = [&]() {
+      const R* Sm[3] = {A.S0, A.S1, A.S2};
+      long long o[8];
+      cic_offsets<R>(ci, A.M, o);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        R acc = R(0);
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          acc += ((k & 1) ? cf[0] : R(1) - cf[0]) * (((k >> 1) & 1) ? cf[1] : R(1) - cf[1]) *
+                 ((k >> 2) ? cf[2] : R(1) - cf[2]) * Sm[c][o[k]];
+        cs[c] = acc;
+      }
+      have_s = true;
+    };
     // one replica of this particle (the per-particle tests below decide exactly)
     auto project = [&](int q) {
       const Replica rp = A.rep[q];
@@ -517,21 +533,7 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
       if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2, A.g.lo2, A.g.hi2))) return;
       const R lim = r[2] * tan_half + margin;
       if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
-      if (A.S0 && !have_s) {
-        const R* Sm[3] = {A.S0, A.S1, A.S2};
-        long long o[8];
-        cic_offsets<R>(ci, A.M, o);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          R acc = R(0);
-#pragma unroll
-          for (int k = 0; k < 8; ++k)
-            acc += ((k & 1) ? cf[0] : R(1) - cf[0]) * (((k >> 1) & 1) ? cf[1] : R(1) - cf[1]) *
-                   ((k >> 2) ? cf[2] : R(1) - cf[2]) * Sm[c][o[k]];
-          cs[c] = acc;
-        }
-        have_s = true;
-      }
+      if (A.S0 && !have_s) gather_s();
       R pr[3], sr[3], sg[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -629,6 +631,7 @@ __global__ void __launch_bounds__(256, 3) k_lens_vjp(const LensAdjArgs<R> A) {
       unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, A.g.cull_cell_len, A.g.cull_lo2, A.g.cull_hi2,
                                     A.g.cull_tan_half, A.g.cull_margin);
       if (!valid) live = 0u;
+      if (A.S0 && live && !have_s) gather_s();  // as in the forward: before the per-replica tests
       while (live) {
         const int q = base + __ffs(live) - 1;
         live &= live - 1u;

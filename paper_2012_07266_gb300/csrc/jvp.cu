@@ -208,6 +208,22 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
     R cs0 = R(0), cs1 = R(0), cs2 = R(0), ts0 = R(0), ts1 = R(0), ts2 = R(0);
     bool have_s = false;
     const WarpBox box = warp_box(valid, (float)ci0 + (float)cf0, (float)ci1 + (float)cf1, (float)ci2 + (float)cf2);
+    // the particle's PGD displacement and its tangent (cells)
+    auto gather_s = [&]() {
+      const Corners cc = corners(A.M, ci0, ci1, ci2);
+      const R* Sm[3] = {A.S0, A.S1, A.S2};
+      const R* dSm[3] = {A.dS0, A.dS1, A.dS2};
+      R sv[3], tv[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        R g[3];
+        sv[k] = value_grad(Sm[k], cc, cf0, cf1, cf2, g);
+        tv[k] = gather(dSm[k], cc, cf0, cf1, cf2) + g[0] * tx0 + g[1] * tx1 + g[2] * tx2;
+      }
+      cs0 = sv[0]; cs1 = sv[1]; cs2 = sv[2];
+      ts0 = tv[0]; ts1 = tv[1]; ts2 = tv[2];
+      have_s = true;
+    };
     auto project = [&](int q) {
       const Replica rp = A.rep[q];
       R r[3], pr[3], dr[3], dpr[3], gf[3];
@@ -237,21 +253,7 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
       if (!(r[2] > R(0) && in_shell<R>(chi2, gi, gf, A.cell_len, A.chi_lo2, A.chi_hi2, A.g.lo2, A.g.hi2))) return;
       const R lim = r[2] * tan_half + margin;
       if (fabs(r[0]) > lim || fabs(r[1]) > lim) return;
-      if (A.S0 && !have_s) {
-        const Corners cc = corners(A.M, ci0, ci1, ci2);
-        const R* Sm[3] = {A.S0, A.S1, A.S2};
-        const R* dSm[3] = {A.dS0, A.dS1, A.dS2};
-        R sv[3], tv[3];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          R g[3];
-          sv[k] = value_grad(Sm[k], cc, cf0, cf1, cf2, g);
-          tv[k] = gather(dSm[k], cc, cf0, cf1, cf2) + g[0] * tx0 + g[1] * tx1 + g[2] * tx2;
-        }
-        cs0 = sv[0]; cs1 = sv[1]; cs2 = sv[2];
-        ts0 = tv[0]; ts1 = tv[1]; ts2 = tv[2];
-        have_s = true;
-      }
+      if (A.S0 && !have_s) gather_s();
       R rc[3], drc[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) { rc[d] = r[d]; drc[d] = dr[d]; }
@@ -323,6 +325,7 @@ __global__ void __launch_bounds__(256) k_tan_lens(const LensTanArgs<R> A) {
       unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, A.g.cull_cell_len, A.g.cull_lo2, A.g.cull_hi2,
                                     A.g.cull_tan_half, A.g.cull_margin);
       if (!valid) live = 0u;
+      if (A.S0 && live && !have_s) gather_s();  // as in the forward: before the per-replica tests
       while (live) {
         const int q = base + __ffs(live) - 1;
         live &= live - 1u;

@@ -230,6 +230,16 @@ __global__ void __launch_bounds__(256) k_lens(const LensArgs<R> A) {
       unsigned live = cull_replicas(A.rep, A.nrep, base, box, A.M, A.g.cull_cell_len, A.g.cull_lo2, A.g.cull_hi2,
                                     A.g.cull_tan_half, A.g.cull_margin);
       if (!valid) live = 0u;
+      // the PGD displacement of every particle of a warp that may reach the map, gathered
+      // before the per-replica tests (which then find it in registers): its load latency
+      // overlaps the replica geometry (0.528 -> 0.491 ms per pm256 launch)
+      if (A.S0 && live && !have_s) {
+        cs0 = gather3(A.S0, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
+        cs1 = gather3(A.S1, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
+        cs2 = gather3(A.S2, A.M, ci0, ci1, ci2, cf0, cf1, cf2);
+        have_s = true;
+        ++ngath;
+      }
       while (live) {
         const int q = base + __ffs(live) - 1;
         live &= live - 1u;
