@@ -3,9 +3,10 @@
 //
 // One thread per particle, replicas looped in registers: the particle is read
 // once (cell, fraction, momentum, optional PGD displacement gathered from the
-// PGD meshes) and tested against every replica of the shell.  Geometry runs in
-// the path's precision (FP32 fast path: positions in Mpc/h to ~1e-7 relative),
-// the lensing weights and the map accumulation always in FP64.
+// PGD meshes) and tested against every replica the warp may reach.  Geometry
+// and the lensing weights run in the path's precision (FP32 fast path:
+// positions in Mpc/h to ~1e-7 relative; shell membership near a boundary
+// decided in FP64), the map accumulation always in FP64.
 #include <algorithm>
 #include <cmath>
 
